@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Benchmark of the CB-ESSFM DBP hot path on GB300.
+
+Workload (one step = one ``cbessfm_backpropagate`` launch over the whole batch): 5 channels x
+64 GBd DP-64QAM at 100 GHz spacing, 2 samples/symbol over the WDM band (R = 640 GS/s),
+2^16 symbols per channel, 7 realizations (launch powers -2..+4 dBm), backpropagated over
+15 x 80 km with N_sb = 5 coupled subbands, N_st = 15 asymmetric steps (rho = 0.3), 11 taps per
+band pair, N' = 1024, N'_ov = 256.  Metric: 2D symbols per second (2 polarizations x channels x
+symbols).  Inputs are resident in HBM and L2 is flushed (256 MiB write) between timed launches.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload.
+Under torchrun every rank runs its own copy of the workload on its GPU (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import configs, signals  # noqa: E402
+from paper_2409_14489_gb300 import cost  # noqa: E402
+
+WORKLOAD = "c2_wdm15"
+METRIC = "DBP 2D symbols/s on 1 GB300 (plain vs batched/adjoint) at ≤1e-5 rel. err; % HBM roofline"
+UNIT = "2D symbols/s"
+N_SM, FP32_LANES = 152, 128
+FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+KERNEL_SOURCES = ["paper_2409_14489_gb300/csrc/fwd.cu",
+                  "paper_2409_14489_gb300/csrc/device_common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fwd_kernel_c2_traffic.txt")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    txt = open(TRAFFIC_FILE).read()
+    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    m_tr = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+    if not (m_hash and m_tr) or m_hash.group(1) != kernel_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+def workload_setup():
+    wl = configs.get_workload(WORKLOAD)
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    w0 = lk.gamma * signals.effective_length(lk.alpha, lk.span_length)
+    taps = signals.random_taps(wl.seed, d.n_st, d.n_sb, d.ntaps, w0, spread=0.2)
+    return wl, taps
+
+
+def workload_inputs(wl, rank: int = 0):
+    fields = []
+    for k, p_dbm in enumerate(wl.launch_dbm):
+        tx, _ = signals.tx_waveform(wl, p_dbm, seed=wl.seed * 1000 + k + 7919 * rank)
+        fields.append(tx)
+    return np.stack(fields).astype(np.complex64)
+
+
+def config_dict(wl):
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    return {
+        "workload": (f"{wl.name}: {sig.n_ch} ch x {sig.baud / 1e9:g} GBd DP-{sig.qam}QAM, "
+                     f"{lk.n_spans}x{lk.span_length / 1e3:g} km, R={sig.sample_rate / 1e9:g} GS/s, "
+                     f"N_sb={d.n_sb}, N_st={d.n_st}, rho={d.ratio}, {d.ntaps} taps, "
+                     f"N'={d.n_fft}, N'_ov={d.overlap}, {wl.batch} realizations x "
+                     f"{sig.n_samples} samples"),
+        "batch": wl.batch,
+        "n_samples": sig.n_samples,
+        "sym2d_per_step": wl.batch * sig.sym2d_per_realization,
+        "l2": "flushed between timed launches (256 MiB write); inputs 73 MB",
+        "parallelism": "one process per GPU, independent workload per rank",
+    }
+
+
+def flops_per_2d(wl) -> float:
+    d = wl.dbp
+    n = wl.signal.n_samples / (wl.signal.sym2d_per_realization / 2.0)   # samples per 4D symbol
+    return cost.cbessfm_flops_per_2d(d.n_block, d.n_ov_total, n, d.n_sb, d.n_st)
+
+
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(device_index), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, smax, reasons = [], None, set()
+        for ln in out.strip().splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------
+def cpu_baseline(wl, taps, fields, budget_s: float = 12.0):
+    """The FP64 oracle (mode B) on whole overlap-and-save blocks of realization 0, for about
+    ``budget_s`` seconds; returns (2D symbols/s, description)."""
+    from oracle import dbp as odbp
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    p = odbp.ChainParams(beta2=lk.beta2, sample_rate=sig.sample_rate, link_length=lk.length,
+                         n_sb=d.n_sb, ratio=d.ratio,
+                         taps=taps.astype(np.float32).astype(np.float64))
+    field = fields[0].astype(np.complex128)
+    V = d.n_block - d.n_ov_total
+    n_blocks = -(-sig.n_samples // V)
+    sym_per_sample = sig.sym2d_per_realization / sig.n_samples
+    t0 = time.perf_counter()
+    done = 0
+    while True:
+        odbp.dbp_mode_b(field, p, d.n_fft, d.overlap, blocks=[done % n_blocks])
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    sym = done * V * sym_per_sample
+    return sym / el, f"{done} blocks x {V} valid samples of realization 0 ({el:.1f} s, FP64 numpy)"
+
+
+def run_reference(args, wl, taps):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    fields = workload_inputs(wl)[:1]
+    from oracle import dbp as odbp
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    p = odbp.ChainParams(beta2=lk.beta2, sample_rate=sig.sample_rate, link_length=lk.length,
+                         n_sb=d.n_sb, ratio=d.ratio, taps=taps.astype(np.float32).astype(np.float64))
+    V = d.n_block - d.n_ov_total
+    n_blocks = -(-sig.n_samples // V)
+    blocks_per_step = 4
+    sym_per_sample = sig.sym2d_per_realization / sig.n_samples
+    f = fields[0].astype(np.complex128)
+    for w in range(args.warmup):
+        odbp.dbp_mode_b(f, p, d.n_fft, d.overlap, blocks=[w % n_blocks])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        odbp.dbp_mode_b(f, p, d.n_fft, d.overlap,
+                        blocks=[(k * blocks_per_step + i) % n_blocks for i in range(blocks_per_step)])
+    el = time.perf_counter() - t0
+    value = args.steps * blocks_per_step * V * sym_per_sample / el
+    sample = f"{blocks_per_step} overlap-and-save blocks ({V} valid samples each) per step"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+def run_gpu(args, wl, taps):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2409_14489_gb300 import cbessfm
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    fields = workload_inputs(wl, rank)
+    link = cbessfm.make_link(lk.beta2, lk.span_length, lk.n_spans, sig.sample_rate)
+    plan = cbessfm.Plan(link, d.n_sb, d.n_st, d.ratio, taps.astype(np.float32), d.n_fft,
+                        d.overlap)
+    stream = torch.cuda.current_stream()
+    x = torch.from_numpy(fields).cuda()
+    y = torch.empty_like(x)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    sym_per_step = wl.batch * sig.sym2d_per_realization
+
+    for _ in range(args.warmup):
+        plan.backpropagate(x, y)
+    torch.cuda.synchronize()
+    if plan.status() != 0:
+        raise RuntimeError("device status reported an error during warm-up")
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        plan.backpropagate(x, y)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clocks = sampler.stop()
+    kernel_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(kernel_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    if plan.status() != 0:
+        raise RuntimeError("device status reported an error during the timed launches")
+
+    # ---- end to end: pinned host buffers, H2D + launch + D2H inside the timed region ------
+    h_in = torch.from_numpy(fields).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        x.copy_(h_in, non_blocking=True)
+        plan.backpropagate(x, y)
+        h_out.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        x.copy_(h_in, non_blocking=True)
+        plan.backpropagate(x, y)
+        h_out.copy_(y, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        pk, pk_kind = peaks()
+        sm_mhz = float(pk.get("sm_max_mhz", FALLBACK["sm_max_mhz"]))
+        fp32_peak = N_SM * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s
+        avg_s = total_ms / args.steps / 1e3
+        flops_launch = flops_per_2d(wl) * sym_per_step
+        achieved = flops_launch / avg_s / 1e12
+        bytes_launch = 2 * fields.nbytes                                   # read + write once
+        hbm = float(pk.get("hbm_gbs", FALLBACK["hbm_gbs"]))
+        value = world * sym_per_step * args.steps / (total_ms / 1e3)
+        cpu_val, cpu_desc = cpu_baseline(wl, taps, fields)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded WDM DP-64QAM transmit waveforms, random-perturbed taps)",
+            "config": config_dict(wl),
+            "roofline": {
+                "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": recorded_traffic(),
+                "peak_source": (f"FP32: {N_SM} SMs x {FP32_LANES} lanes x 2 flop x "
+                                f"{sm_mhz:g} MHz ({pk_kind} max SM clock)"),
+                "flops_per_launch": flops_launch,
+                "flops_model": "paper RM + RA per 2D symbol (Eq. (costRM) and its RA companion)",
+                "hbm": {"bytes_per_launch": bytes_launch,
+                        "achieved_gbs": bytes_launch / avg_s / 1e9, "peak_gbs": hbm,
+                        "frac": bytes_launch / avg_s / 1e9 / hbm,
+                        "peak_kind": f"{pk_kind} copy bandwidth"},
+            },
+            "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": cpu_desc},
+            "e2e": {"value": world * sym_per_step * e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
+                    "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)       # at least 3 untimed warm-up steps, reported as run
+    wl, taps = workload_setup()
+    if args.impl == "reference":
+        return run_reference(args, wl, taps)
+    return run_gpu(args, wl, taps)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

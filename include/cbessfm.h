@@ -1,0 +1,137 @@
+/*
+ * cbessfm.h -- C-ABI of the GB300 (sm_103a) CB-ESSFM digital backpropagation library.
+ *
+ * The library implements the coupled-band enhanced split-step Fourier method of
+ * "A New Twist on Low-Complexity Digital Backpropagation" (Civelli, Jana, Forestieri,
+ * Secondini): overlap-and-save blocks (Sec. III-A, Fig. 2) of a dual-polarization field, two
+ * full-band FFTs, a DEMUX into N_sb subbands, N_st steps of {GVD, NLPR} (Figs. 3-4) with the
+ * nonlinear phase of Eq. (NLPR-multiband-2pol), asymmetric steps with splitting ratio rho
+ * (Sec. III-C), a final GVD, MUX and two inverse FFTs.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Units are SI.  A 4D sample is four float32 values (x.re, x.im, y.re, y.im), 16 bytes,
+ *    16-byte aligned; a field is [batch][n_samples] such samples, contiguous.
+ *  - The input is one period of a periodic sequence: overlap-and-save blocks wrap circularly.
+ *  - Taps are the *effective* filter coefficients w[s][i][l][m + N_c] applied as
+ *        theta_i[k] = sum_l sum_{m=-N_c}^{N_c} w[s][i][l][m + N_c] * P_l[(k - m) mod N']
+ *    with P_l = |x_l|^2 + |y_l|^2 (the 3/2 XPM degeneracy factor of Eq. (NLPR-multiband-2pol)
+ *    is folded into w[s][i][l] for l != i).  The rotation is exp(+j theta_i) on both
+ *    polarizations and the GVD of subband bin f is exp(+j 2 pi^2 beta2 dz f^2) (Sec. III-A).
+ *  - Device pointers are CUDA device addresses owned by the caller unless stated otherwise.
+ *    The plan owns its device tables.  Every call is asynchronous on `stream` (a cudaStream_t;
+ *    NULL is the legacy default stream) unless stated otherwise.
+ *  - Errors: every call returns a cbessfm_status; nothing aborts and no C++ exception crosses
+ *    the ABI.  cbessfm_last_error() returns a thread-local message for the last failure.
+ *  - A plan is read-only during launches, so concurrent launches with one plan on different
+ *    streams are safe; cbessfm_set_coeffs / cbessfm_set_ratio must not race with launches that
+ *    use the plan.
+ */
+#ifndef CBESSFM_H_
+#define CBESSFM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so this header does not need the CUDA headers. */
+typedef struct CUstream_st* cbessfm_stream;
+
+typedef enum {
+    CBESSFM_OK = 0,
+    CBESSFM_ERR_INVALID_ARG = 1,     /* a parameter is out of range or a pointer is NULL      */
+    CBESSFM_ERR_UNSUPPORTED = 2,     /* valid, but not supported by this build (size limits)   */
+    CBESSFM_ERR_ALIAS = 3,           /* output overlaps input                                  */
+    CBESSFM_ERR_CUDA = 4,            /* a CUDA runtime call failed                             */
+    CBESSFM_ERR_OOM = 5,             /* device or host allocation failed                       */
+    CBESSFM_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up (see get_status)    */
+    CBESSFM_ERR_NOT_IMPLEMENTED = 7
+} cbessfm_status;
+
+/* Fiber link being backpropagated (Sec. II-A, Eq. (NLSE); Sec. IV-A). */
+typedef struct {
+    double beta2;        /* group-velocity dispersion, s^2/m (e.g. -21.7e-27)                 */
+    double gamma;        /* nonlinear coefficient, 1/(W m); informational (taps carry it)     */
+    double alpha;        /* power attenuation, 1/m; informational (taps carry it)             */
+    double span_length;  /* m                                                                 */
+    int    n_spans;      /* link length = n_spans * span_length                               */
+    double sample_rate;  /* full-band sampling rate R, Hz                                     */
+} cbessfm_link;
+
+typedef enum {
+    CBESSFM_C64 = 0,     /* complex64 input/output (float4 per 4D sample)                    */
+    CBESSFM_F16x4 = 1,   /* four fp16 per 4D sample, FP32 arithmetic inside                 */
+    CBESSFM_BF16x4 = 2   /* four bf16 per 4D sample, FP32 arithmetic inside                 */
+} cbessfm_storage;
+
+typedef struct cbessfm_plan cbessfm_plan;
+
+/*
+ * cbessfm_plan_create -- build a DBP plan (Sec. III-A; asymmetric steps Sec. III-C).
+ *   link      host pointer to the link description; L_step = n_spans * span_length / steps.
+ *   bands     N_sb >= 1 subbands.
+ *   steps     N_st >= 0 steps (0 = dispersion compensation over the whole link, EDC).
+ *   ratio     splitting ratio rho in [0, 1]: first GVD (1 - rho) L_step, interior GVDs L_step,
+ *             last GVD rho L_step.
+ *   coeffs    host float array [steps][bands][bands][ntaps] of effective taps (may be NULL when
+ *             steps == 0); copied into the plan.
+ *   ntaps     2 N_c + 1, odd, 1 <= ntaps <= n_fft / 2.
+ *   n_fft     N' = per-subband FFT size, a power of two in [16, 2048]; block N = bands * N'.
+ *   overlap   N'_ov = per-subband overlap, even, 0 <= overlap < n_fft; N_ov = bands * N'_ov
+ *             samples are shared by neighbouring blocks, N_ov / 2 dropped on each side
+ *             (Sec. III-A, Fig. 2).
+ *   storage   sample storage type of in/out.
+ *   out       receives the plan.
+ * Synchronous.  Builds the FP64-derived tables (GVD phases reduced modulo 2 pi, FFT twiddles)
+ * on the current device.  Returns INVALID_ARG for out-of-range values, UNSUPPORTED when the
+ * block does not fit one SM's shared memory.
+ */
+cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int steps, double ratio,
+                                   const float* coeffs, int ntaps, int n_fft, int overlap,
+                                   cbessfm_storage storage, cbessfm_plan** out);
+
+/* Release the plan and its device tables.  Synchronous; NULL is accepted. */
+cbessfm_status cbessfm_plan_destroy(cbessfm_plan* plan);
+
+/*
+ * cbessfm_set_coeffs -- replace the taps (layout as in plan_create).
+ *   on_device = 0: `coeffs` is a host array (the call synchronizes the copy);
+ *   on_device = 1: a device array, copied asynchronously on `stream`.
+ */
+cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int on_device,
+                                  cbessfm_stream stream);
+
+/* cbessfm_set_ratio -- change rho (Sec. III-C); rebuilds the first and last GVD tables with an
+ * FP64 kernel on `stream`. */
+cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_stream stream);
+
+/*
+ * cbessfm_backpropagate -- run the DBP chain (Sec. III-A) on `batch` independent sequences.
+ *   in, out    device arrays [batch][n_samples] 4D samples in the plan's storage type; out
+ *              must not overlap in (ALIAS).
+ *   n_samples  L >= 1 samples per sequence (one period); any length, blocks wrap circularly.
+ * One kernel launch: each CTA stages its overlap-and-save blocks into shared memory with the
+ * Tensor Memory Accelerator and runs the whole chain on chip.
+ */
+cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, void* out,
+                                     int64_t n_samples, int batch, cbessfm_stream stream);
+
+/*
+ * cbessfm_get_status -- synchronize `stream`, then read and clear the plan's device status word
+ * (bit 0: a bounded wait for a shared-memory copy gave up -> CBESSFM_ERR_TIMEOUT).
+ */
+cbessfm_status cbessfm_get_status(const cbessfm_plan* plan, cbessfm_stream stream);
+
+/* Thread-local description of the last error returned on this thread ("" if none). */
+const char* cbessfm_last_error(void);
+
+/* Library version string. */
+const char* cbessfm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBESSFM_H_ */

@@ -1,0 +1,192 @@
+"""Thin Python binding of ``libcbessfm.so`` (declared in ``include/cbessfm.h``).
+
+Argument marshalling only: every step of the DBP chain runs in the library's CUDA kernels.
+PyTorch provides device memory and streams.  Importing this module loads the library and raises
+``ImportError`` if it has not been built -- there is no CPU fallback.
+
+Field tensors are complex64 of shape ``(L, 2)`` or ``(batch, L, 2)`` (polarization-minor), which
+is exactly the library's float4-per-sample layout.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+_LIB_PATH = _build.LIB
+
+
+class CBESSFMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"cbessfm status {status} ({STATUS_NAMES.get(status, '?')}): {message}")
+        self.status = status
+
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "ALIAS", 4: "CUDA", 5: "OOM",
+                6: "TIMEOUT", 7: "NOT_IMPLEMENTED"}
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_ALIAS, ERR_CUDA, ERR_OOM, ERR_TIMEOUT, \
+    ERR_NOT_IMPLEMENTED = range(8)
+STORAGE_C64, STORAGE_F16X4, STORAGE_BF16X4 = 0, 1, 2
+
+
+class LinkStruct(ctypes.Structure):
+    _fields_ = [("beta2", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("span_length", ctypes.c_double),
+                ("n_spans", ctypes.c_int), ("sample_rate", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is not built: run __graft_entry__.build() "
+                          "(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    c_int, c_double, c_void_p, c_int64 = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64
+    P = ctypes.c_void_p
+    lib.cbessfm_plan_create.argtypes = [ctypes.POINTER(LinkStruct), c_int, c_int, c_double,
+                                        ctypes.POINTER(ctypes.c_float), c_int, c_int, c_int, c_int,
+                                        ctypes.POINTER(P)]
+    lib.cbessfm_plan_create.restype = c_int
+    lib.cbessfm_plan_destroy.argtypes = [P]
+    lib.cbessfm_plan_destroy.restype = c_int
+    lib.cbessfm_set_coeffs.argtypes = [P, c_void_p, c_int, c_void_p]
+    lib.cbessfm_set_coeffs.restype = c_int
+    lib.cbessfm_set_ratio.argtypes = [P, c_double, c_void_p]
+    lib.cbessfm_set_ratio.restype = c_int
+    lib.cbessfm_backpropagate.argtypes = [P, c_void_p, c_void_p, c_int64, c_int, c_void_p]
+    lib.cbessfm_backpropagate.restype = c_int
+    lib.cbessfm_get_status.argtypes = [P, c_void_p]
+    lib.cbessfm_get_status.restype = c_int
+    lib.cbessfm_last_error.argtypes = []
+    lib.cbessfm_last_error.restype = ctypes.c_char_p
+    lib.cbessfm_version.argtypes = []
+    lib.cbessfm_version.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise CBESSFMError(status, _lib.cbessfm_last_error().decode())
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def make_link(beta2: float, span_length: float, n_spans: int, sample_rate: float,
+              gamma: float = 0.0, alpha: float = 0.0) -> LinkStruct:
+    return LinkStruct(beta2, gamma, alpha, span_length, n_spans, sample_rate)
+
+
+class Plan:
+    """A CB-ESSFM DBP plan (``cbessfm_plan_create``).
+
+    ``coeffs``: effective taps ``[steps][bands][bands][ntaps]`` (float32, host).
+    """
+
+    def __init__(self, link: LinkStruct, bands: int, steps: int, ratio: float, coeffs,
+                 n_fft: int, overlap: int, storage: int = STORAGE_C64):
+        ntaps = 1
+        cptr = None
+        self._coeffs = None
+        if steps > 0:
+            c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float32))
+            if c.ndim != 4 or c.shape[:3] != (steps, bands, bands):
+                raise ValueError(f"coeffs must have shape ({steps}, {bands}, {bands}, ntaps)")
+            ntaps = int(c.shape[3])
+            self._coeffs = c
+            cptr = c.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        elif coeffs is not None and np.asarray(coeffs).ndim == 4:
+            ntaps = int(np.asarray(coeffs).shape[3])
+        self._h = ctypes.c_void_p()
+        self.link = link
+        self.bands, self.steps, self.ratio = bands, steps, ratio
+        self.ntaps, self.n_fft, self.overlap, self.storage = ntaps, n_fft, overlap, storage
+        _check(_lib.cbessfm_plan_create(ctypes.byref(link), bands, steps, float(ratio), cptr,
+                                        ntaps, n_fft, overlap, storage, ctypes.byref(self._h)))
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    @property
+    def block(self) -> int:
+        return self.bands * self.n_fft
+
+    @property
+    def valid(self) -> int:
+        return self.bands * (self.n_fft - self.overlap)
+
+    def n_blocks(self, n_samples: int) -> int:
+        return -(-n_samples // self.valid)
+
+    def backpropagate(self, x, out=None, stream=None):
+        """Run DBP on a complex64 CUDA tensor of shape (L, 2) or (batch, L, 2)."""
+        import torch
+        if not (x.is_cuda and x.dtype == torch.complex64 and x.is_contiguous()):
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        if x.dim() == 2:
+            batch, L = 1, x.shape[0]
+        elif x.dim() == 3:
+            batch, L = x.shape[0], x.shape[1]
+        else:
+            raise ValueError("x must have shape (L, 2) or (batch, L, 2)")
+        if x.shape[-1] != 2:
+            raise ValueError("last dimension must be the two polarizations")
+        if out is None:
+            out = torch.empty_like(x)
+        _check(_lib.cbessfm_backpropagate(self._h, x.data_ptr(), out.data_ptr(), L, batch,
+                                          _stream_handle(stream)))
+        return out
+
+    def backpropagate_ptr(self, in_ptr: int, out_ptr: int, n_samples: int, batch: int,
+                          stream_handle: int):
+        """Raw-pointer form of ``cbessfm_backpropagate`` (device addresses)."""
+        _check(_lib.cbessfm_backpropagate(self._h, in_ptr, out_ptr, n_samples, batch,
+                                          stream_handle))
+
+    def set_coeffs(self, coeffs, stream=None):
+        import torch
+        if isinstance(coeffs, torch.Tensor) and coeffs.is_cuda:
+            c = coeffs.detach().to(torch.float32).contiguous()
+            _check(_lib.cbessfm_set_coeffs(self._h, c.data_ptr(), 1, _stream_handle(stream)))
+            return c
+        c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float32))
+        _check(_lib.cbessfm_set_coeffs(self._h, c.ctypes.data, 0, _stream_handle(stream)))
+        return c
+
+    def set_ratio(self, ratio: float, stream=None):
+        _check(_lib.cbessfm_set_ratio(self._h, float(ratio), _stream_handle(stream)))
+        self.ratio = float(ratio)
+
+    def status(self, stream=None) -> int:
+        """Synchronize and return the device status as a cbessfm_status value (0 = OK)."""
+        return _lib.cbessfm_get_status(self._h, _stream_handle(stream))
+
+    def close(self):
+        if self._h:
+            _lib.cbessfm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def version() -> str:
+    return _lib.cbessfm_version().decode()

@@ -1,0 +1,327 @@
+// api.cu -- C-ABI entry points: plan construction (FP64 tables), validation, launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+struct cbessfm_plan {
+    cbessfm::PlanImpl impl;
+};
+
+namespace cbessfm {
+namespace {
+
+thread_local std::string g_last_error;
+
+cbessfm_status fail(cbessfm_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+cbessfm_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(e == cudaErrorMemoryAllocation ? CBESSFM_ERR_OOM : CBESSFM_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+constexpr int kMaxDynSmem = 226 * 1024;     // 227 KB opt-in minus room for static shared memory
+constexpr int kMaxThreads = 640;
+constexpr int kMaxG = 16;
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+void free_plan(PlanImpl& p) {
+    cudaFree(p.d_gvd);
+    cudaFree(p.d_kdisp);
+    cudaFree(p.d_mix_tw);
+    cudaFree(p.d_fft_tw);
+    cudaFree(p.d_taps);
+    cudaFree(p.d_status);
+    p.d_gvd = nullptr;
+    p.d_kdisp = nullptr;
+    p.d_mix_tw = nullptr;
+    p.d_fft_tw = nullptr;
+    p.d_taps = nullptr;
+    p.d_status = nullptr;
+}
+
+// [n_st][n_sb][n_sb][ntaps] -> [n_st][n_sb][n_sb][ntaps_pad] with zero padding at the end
+std::vector<float> pack_taps(const PlanImpl& p, const float* coeffs) {
+    const size_t rows = (size_t)p.n_st * p.n_sb * p.n_sb;
+    std::vector<float> out(rows * p.ntaps_pad, 0.f);
+    for (size_t r = 0; r < rows; ++r)
+        for (int m = 0; m < p.ntaps; ++m) out[r * p.ntaps_pad + m] = coeffs[r * p.ntaps + m];
+    return out;
+}
+
+}  // namespace
+
+ChainArgs make_chain_args(const PlanImpl& p) {
+    ChainArgs a{};
+    a.n_sb = p.n_sb;
+    a.n_st = p.n_st;
+    a.N = p.N;
+    a.n_ov = p.n_ov;
+    a.V = p.V;
+    a.G = p.G;
+    a.nc = p.nc;
+    a.ntaps_pad = p.ntaps_pad;
+    a.nchunks = p.nchunks;
+    a.H = p.H;
+    a.p_off = p.p_off;
+    a.pstride = p.pstride;
+    a.region_bytes = p.region_bytes;
+    a.gvd = p.d_gvd;
+    a.mix_tw = p.d_mix_tw;
+    a.fft_tw = p.d_fft_tw;
+    a.taps = p.d_taps;
+    a.status = p.d_status;
+    return a;
+}
+
+}  // namespace cbessfm
+
+using namespace cbessfm;
+
+extern "C" {
+
+const char* cbessfm_last_error(void) { return g_last_error.c_str(); }
+
+const char* cbessfm_version(void) { return "cbessfm-gb300 0.1 (sm_103a)"; }
+
+cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int steps, double ratio,
+                                   const float* coeffs, int ntaps, int n_fft, int overlap,
+                                   cbessfm_storage storage, cbessfm_plan** out) {
+    g_last_error.clear();
+    if (out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (link == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "link is NULL");
+    if (!(link->sample_rate > 0.0) || !std::isfinite(link->sample_rate))
+        return fail(CBESSFM_ERR_INVALID_ARG, "sample_rate must be positive and finite");
+    if (!(link->span_length > 0.0) || link->n_spans < 1)
+        return fail(CBESSFM_ERR_INVALID_ARG, "span_length must be > 0 and n_spans >= 1");
+    if (!std::isfinite(link->beta2)) return fail(CBESSFM_ERR_INVALID_ARG, "beta2 not finite");
+    if (bands < 1 || bands > 16) return fail(CBESSFM_ERR_INVALID_ARG, "bands must be in [1, 16]");
+    if (steps < 0 || steps > 4096) return fail(CBESSFM_ERR_INVALID_ARG, "steps must be in [0, 4096]");
+    if (!(ratio >= 0.0 && ratio <= 1.0)) return fail(CBESSFM_ERR_INVALID_ARG, "ratio must be in [0, 1]");
+    if (!is_pow2(n_fft) || n_fft < 16 || n_fft > 2048)
+        return fail(CBESSFM_ERR_INVALID_ARG, "n_fft must be a power of two in [16, 2048]");
+    if (ntaps < 1 || (ntaps & 1) == 0 || ntaps > n_fft / 2)
+        return fail(CBESSFM_ERR_INVALID_ARG, "ntaps must be odd and in [1, n_fft/2]");
+    if (overlap < 0 || (overlap & 1) || overlap >= n_fft)
+        return fail(CBESSFM_ERR_INVALID_ARG, "overlap must be even and in [0, n_fft)");
+    if (steps > 0 && coeffs == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "coeffs is NULL");
+    if (storage != CBESSFM_C64)
+        return fail(CBESSFM_ERR_NOT_IMPLEMENTED, "only complex64 storage is built");
+
+    PlanImpl p;
+    p.link = *link;
+    p.n_sb = bands;
+    p.n_st = steps;
+    p.ratio = ratio;
+    p.ntaps = ntaps;
+    p.n_fft = n_fft;
+    p.overlap = overlap;
+    p.storage = storage;
+    p.N = bands * n_fft;
+    p.n_ov = bands * overlap;
+    p.V = p.N - p.n_ov;
+    p.step_length = steps > 0 ? link->span_length * link->n_spans / steps : 0.0;
+    p.nc = (ntaps - 1) / 2;
+    p.nchunks = (ntaps + 3) / 4;
+    p.ntaps_pad = 4 * p.nchunks;
+    p.H = round_up(p.nc + 4, 4);
+    p.p_off = ((3 - p.nc) % 4 + 4) % 4;
+    p.pstride = n_fft + 2 * p.H + 8;
+
+    const int tpf = n_fft / 16;
+    const int tb = 2 * bands * tpf;                 // one polarization per thread
+    if (tb > kMaxThreads)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "bands * n_fft / 16 = %d threads exceeds %d", tb,
+                    kMaxThreads);
+    const int need_stage = 16 * p.N;
+    const int need_exch = 16 * xpad_len(p.N);
+    const int need_fir = 4 * bands * p.pstride + 8 * bands * n_fft;   // P rows + (cos, sin)
+    p.region_bytes = round_up(std::max(need_stage, std::max(need_exch, need_fir)), 128);
+    if (p.region_bytes > kMaxDynSmem)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "block of %d samples needs %d B of shared memory",
+                    p.N, p.region_bytes);
+    // G blocks per CTA: about 256 threads, whole warps (G * tb multiple of 32), shared memory and
+    // named-barrier ids (1 + g * bands + i <= 15 when groups span more than one warp).
+    int granule = 1;
+    while ((granule * tb) % 32 != 0) granule *= 2;
+    int G = std::max(granule, (256 / tb) / granule * granule);
+    G = std::min(G, kMaxG);
+    while (G > granule && (G * p.region_bytes > kMaxDynSmem || G * tb > kMaxThreads ||
+                           (2 * tpf > 32 && G * bands > 15)))
+        G -= granule;
+    if (G * p.region_bytes > kMaxDynSmem || G * tb > kMaxThreads || (2 * tpf > 32 && G * bands > 15))
+        return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape fits bands = %d, n_fft = %d", bands, n_fft);
+    p.G = G;
+    p.threads = G * tb;
+
+    cudaError_t e = cudaGetDevice(&p.device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+
+    // ---- FP64 tables on the host: FFT pass twiddles and DEMUX/MUX twiddles -------------------
+    std::vector<float2> fft_tw(std::max(1, fft_tw_size(n_fft)));
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int pass = 1; pass < fft_npasses(n_fft); ++pass) {
+        const int R = fft_radix(n_fft, pass), NS = fft_ns(n_fft, pass);
+        const int off = fft_tw_offset(n_fft, pass);
+        for (int r = 1; r < R; ++r)
+            for (int a = 0; a < NS; ++a) {
+                const long long num = (long long)a * r;           // < NS R
+                const double ang = -two_pi * (double)num / (double)(NS * R);
+                fft_tw[off + (r - 1) * NS + a] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+            }
+    }
+    std::vector<float2> mix_tw((size_t)bands * p.N);
+    for (int r = 0; r < bands; ++r)
+        for (int K = 0; K < p.N; ++K) {
+            const long long num = ((long long)K * r) % p.N;
+            const double ang = -two_pi * (double)num / (double)p.N;
+            mix_tw[(size_t)r * p.N + K] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+
+    const size_t n_taps_dev = std::max<size_t>(1, (size_t)steps * bands * bands * p.ntaps_pad);
+#define CB_TRY(call, what)                    \
+    do {                                      \
+        cudaError_t _e = (call);              \
+        if (_e != cudaSuccess) {              \
+            free_plan(p);                     \
+            return cuda_fail(_e, what);       \
+        }                                     \
+    } while (0)
+    CB_TRY(cudaMalloc(&p.d_gvd, sizeof(float2) * 3 * bands * n_fft), "cudaMalloc(gvd)");
+    CB_TRY(cudaMalloc(&p.d_kdisp, sizeof(float) * bands * n_fft), "cudaMalloc(kdisp)");
+    CB_TRY(cudaMalloc(&p.d_mix_tw, sizeof(float2) * mix_tw.size()), "cudaMalloc(mix)");
+    CB_TRY(cudaMalloc(&p.d_fft_tw, sizeof(float2) * fft_tw.size()), "cudaMalloc(fft tw)");
+    CB_TRY(cudaMalloc(&p.d_taps, sizeof(float) * n_taps_dev), "cudaMalloc(taps)");
+    CB_TRY(cudaMalloc(&p.d_status, sizeof(unsigned int)), "cudaMalloc(status)");
+    CB_TRY(cudaMemset(p.d_status, 0, sizeof(unsigned int)), "cudaMemset(status)");
+    CB_TRY(cudaMemcpy(p.d_fft_tw, fft_tw.data(), sizeof(float2) * fft_tw.size(),
+                      cudaMemcpyHostToDevice), "copy fft twiddles");
+    CB_TRY(cudaMemcpy(p.d_mix_tw, mix_tw.data(), sizeof(float2) * mix_tw.size(),
+                      cudaMemcpyHostToDevice), "copy mix twiddles");
+    CB_TRY(cudaMemset(p.d_taps, 0, sizeof(float) * n_taps_dev), "cudaMemset(taps)");
+    if (steps > 0) {
+        const std::vector<float> packed = pack_taps(p, coeffs);
+        CB_TRY(cudaMemcpy(p.d_taps, packed.data(), sizeof(float) * packed.size(),
+                          cudaMemcpyHostToDevice), "copy taps");
+    }
+    CB_TRY(launch_build_gvd(p, nullptr), "build GVD tables");
+    CB_TRY(prepare_forward(n_fft, kMaxDynSmem), "set shared-memory limit");
+    CB_TRY(cudaDeviceSynchronize(), "plan tables");
+#undef CB_TRY
+
+    cbessfm_plan* plan = new (std::nothrow) cbessfm_plan;
+    if (plan == nullptr) {
+        free_plan(p);
+        return fail(CBESSFM_ERR_OOM, "host allocation of the plan failed");
+    }
+    plan->impl = p;
+    *out = plan;
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_plan_destroy(cbessfm_plan* plan) {
+    g_last_error.clear();
+    if (plan == nullptr) return CBESSFM_OK;
+    cudaDeviceSynchronize();
+    free_plan(plan->impl);
+    delete plan;
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int on_device,
+                                  cbessfm_stream stream) {
+    g_last_error.clear();
+    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    PlanImpl& p = plan->impl;
+    if (p.n_st == 0) return CBESSFM_OK;
+    if (coeffs == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "coeffs is NULL");
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (!on_device) {
+        const std::vector<float> packed = pack_taps(p, coeffs);
+        e = cudaMemcpyAsync(p.d_taps, packed.data(), sizeof(float) * packed.size(),
+                            cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    } else {
+        // row-wise copies of [ntaps] into [ntaps_pad] (padding stays zero)
+        e = cudaMemcpy2DAsync(p.d_taps, sizeof(float) * p.ntaps_pad, coeffs,
+                              sizeof(float) * p.ntaps, sizeof(float) * p.ntaps,
+                              (size_t)p.n_st * p.n_sb * p.n_sb, cudaMemcpyDeviceToDevice, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "set_coeffs");
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_stream stream) {
+    g_last_error.clear();
+    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    if (!(ratio >= 0.0 && ratio <= 1.0)) return fail(CBESSFM_ERR_INVALID_ARG, "ratio must be in [0, 1]");
+    plan->impl.ratio = ratio;
+    const cudaError_t e = launch_build_gvd(plan->impl, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "set_ratio");
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, void* out,
+                                     int64_t n_samples, int batch, cbessfm_stream stream) {
+    g_last_error.clear();
+    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
+    if (n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples must be >= 1");
+    if (batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "batch must be >= 1");
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u)
+        return fail(CBESSFM_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
+    const PlanImpl& p = plan->impl;
+    const unsigned long long bytes = (unsigned long long)n_samples * batch * 16ull;
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
+    if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
+    const long long n_blocks = (n_samples + p.V - 1) / p.V;
+    if (n_blocks * batch > (1ll << 31) - 1)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
+    ChainArgs a = make_chain_args(p);
+    a.in = in;
+    a.out = out;
+    a.L = n_samples;
+    a.batch = batch;
+    a.n_blocks = (int)n_blocks;
+    const cudaError_t e = launch_forward(p, a, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_get_status(const cbessfm_plan* plan, cbessfm_stream stream) {
+    g_last_error.clear();
+    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, plan->impl.d_status, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(plan->impl.d_status, 0, sizeof(h), st);
+    if (e != cudaSuccess) return cuda_fail(e, "get_status");
+    if (h & kStatusTimeout)
+        return fail(CBESSFM_ERR_TIMEOUT, "a bounded device wait for a shared-memory copy gave up");
+    return CBESSFM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,304 @@
+// device_common.cuh -- device building blocks of the CB-ESSFM kernels (sm_103a).
+//
+//  * complex float2 arithmetic,
+//  * radix-2/4/8/16 DFT butterflies on register slots,
+//  * a Stockham FFT of size NP (16..2048) executed by NP/16 threads that each own 16 register
+//    slots of one polarization, exchanging through padded shared memory between passes (the
+//    x and y threads of the same slots sit in adjacent lanes and share the exchange array),
+//  * mbarrier + bulk-copy (TMA) helpers with bounded waits.
+//
+// Slot convention (shared by the forward and adjoint kernels): thread j of an FFT group holds,
+// in slot t (0..15), element j + (NP/16) * t of the sequence, both on the time side and on the
+// frequency side.  The Stockham passes are arranged (radix 16 first and last) so that the first
+// pass reads exactly these elements and the last pass produces exactly these elements; the
+// pointwise steps (dispersion, rotation) therefore run on registers with no reordering.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cbessfm {
+
+// ------------------------------------------------------------------------------------------
+// complex helpers
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 c_mulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+// multiplication by the twiddle w of a forward (INV = false) or inverse (conj(w)) transform
+template <bool INV>
+__device__ __forceinline__ float2 c_tw(float2 a, float2 w) { return INV ? c_mulc(a, w) : c_mul(a, w); }
+// multiplication by -i (forward) or +i (inverse): the quarter-turn twiddle
+template <bool INV>
+__device__ __forceinline__ float2 c_quarter(float2 a) {
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+constexpr float kSqrtHalf = 0.70710678118654752440f;
+constexpr float kCos8 = 0.92387953251128675613f;   // cos(pi/8)
+constexpr float kSin8 = 0.38268343236508977173f;   // sin(pi/8)
+
+// a * exp(-+ j 2 pi m / 16) for the constant exponents a radix-16 butterfly needs
+template <int M, bool INV>
+__device__ __forceinline__ float2 tw16(float2 a) {
+    constexpr int m = M & 15;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (m == 4) {
+        return c_quarter<INV>(a);
+    } else if constexpr (m == 8) {
+        return make_float2(-a.x, -a.y);
+    } else if constexpr (m == 2) {               // (1 -+ j) / sqrt2
+        return INV ? make_float2((a.x - a.y) * kSqrtHalf, (a.x + a.y) * kSqrtHalf)
+                   : make_float2((a.x + a.y) * kSqrtHalf, (a.y - a.x) * kSqrtHalf);
+    } else if constexpr (m == 6) {               // (-1 -+ j) / sqrt2
+        return INV ? make_float2(-(a.x + a.y) * kSqrtHalf, (a.x - a.y) * kSqrtHalf)
+                   : make_float2((a.y - a.x) * kSqrtHalf, -(a.x + a.y) * kSqrtHalf);
+    } else {
+        // general exponent: cos/sin of 2 pi m / 16 from the two octant constants
+        constexpr float cs[16] = {1.f, kCos8, kSqrtHalf, kSin8, 0.f, -kSin8, -kSqrtHalf, -kCos8,
+                                  -1.f, -kCos8, -kSqrtHalf, -kSin8, 0.f, kSin8, kSqrtHalf, kCos8};
+        constexpr float sn[16] = {0.f, kSin8, kSqrtHalf, kCos8, 1.f, kCos8, kSqrtHalf, kSin8,
+                                  0.f, -kSin8, -kSqrtHalf, -kCos8, -1.f, -kCos8, -kSqrtHalf, -kSin8};
+        return c_tw<INV>(a, make_float2(cs[m], -sn[m]));
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// small DFTs (natural order in, natural order out)
+// ------------------------------------------------------------------------------------------
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a0, float2& a1) {
+    const float2 t = a0;
+    a0 = c_add(t, a1);
+    a1 = c_sub(t, a1);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+    const float2 s02 = c_add(a0, a2), d02 = c_sub(a0, a2);
+    const float2 s13 = c_add(a1, a3), d13 = c_quarter<INV>(c_sub(a1, a3));
+    a0 = c_add(s02, s13);
+    a2 = c_sub(s02, s13);
+    a1 = c_add(d02, d13);
+    a3 = c_sub(d02, d13);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+    dft4<INV>(v[0], v[2], v[4], v[6]);           // even samples -> E_k at v[0], v[2], v[4], v[6]
+    dft4<INV>(v[1], v[3], v[5], v[7]);           // odd samples  -> O_k at v[1], v[3], v[5], v[7]
+    const float2 o1 = tw16<2, INV>(v[3]), o2 = tw16<4, INV>(v[5]), o3 = tw16<6, INV>(v[7]);
+    float2 x[8];
+    x[0] = c_add(v[0], v[1]); x[4] = c_sub(v[0], v[1]);
+    x[1] = c_add(v[2], o1);   x[5] = c_sub(v[2], o1);
+    x[2] = c_add(v[4], o2);   x[6] = c_sub(v[4], o2);
+    x[3] = c_add(v[6], o3);   x[7] = c_sub(v[6], o3);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = x[k];
+}
+
+// 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+    dft4<INV>(v[0], v[4], v[8], v[12]);
+    dft4<INV>(v[1], v[5], v[9], v[13]);
+    dft4<INV>(v[2], v[6], v[10], v[14]);
+    dft4<INV>(v[3], v[7], v[11], v[15]);
+    // v[n2 + 4 k1] *= W16^(n2 k1)
+    v[5] = tw16<1, INV>(v[5]);  v[9] = tw16<2, INV>(v[9]);   v[13] = tw16<3, INV>(v[13]);
+    v[6] = tw16<2, INV>(v[6]);  v[10] = tw16<4, INV>(v[10]); v[14] = tw16<6, INV>(v[14]);
+    v[7] = tw16<3, INV>(v[7]);  v[11] = tw16<6, INV>(v[11]); v[15] = tw16<9, INV>(v[15]);
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+    dft4<INV>(v[4], v[5], v[6], v[7]);
+    dft4<INV>(v[8], v[9], v[10], v[11]);
+    dft4<INV>(v[12], v[13], v[14], v[15]);
+    // X[k1 + 4 k2] sits at v[4 k1 + k2]: transpose the 4 x 4 index
+    float2 x[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) x[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = x[k];
+}
+
+// radix-R DFT on slots s, s + S, ..., s + (R-1) S of a 16-slot array (R * S == 16)
+template <int R, int S, bool INV>
+__device__ __forceinline__ void dft_slots(float2 (&a)[16], const int s) {
+    if constexpr (R == 16) {
+        dft16<INV>(a);
+    } else if constexpr (R == 8) {
+        float2 v[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = a[s + r * S];
+        dft8<INV>(v);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) a[s + r * S] = v[r];
+    } else if constexpr (R == 4) {
+        dft4<INV>(a[s], a[s + S], a[s + 2 * S], a[s + 3 * S]);
+    } else if constexpr (R == 2) {
+        dft2<INV>(a[s], a[s + S]);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// FFT pass plan for NP = 16 .. 4096:  16 | 16 x NP/16 | 16 x NP/256 x 16
+// ------------------------------------------------------------------------------------------
+__host__ __device__ constexpr int fft_npasses(int np) { return np <= 16 ? 1 : (np <= 256 ? 2 : 3); }
+__host__ __device__ constexpr int fft_radix(int np, int p) {
+    return p == 0 ? 16 : (np <= 256 ? np / 16 : (p == 1 ? np / 256 : 16));
+}
+__host__ __device__ constexpr int fft_ns(int np, int p) {
+    int ns = 1;
+    for (int q = 0; q < p; ++q) ns *= fft_radix(np, q);
+    return ns;
+}
+// twiddle table of pass p >= 1: [(r - 1) * Ns + a] = W_{Ns R}^(a r), r in [1, R), a in [0, Ns)
+__host__ __device__ constexpr int fft_tw_offset(int np, int p) {
+    int o = 0;
+    for (int q = 1; q < p; ++q) o += (fft_radix(np, q) - 1) * fft_ns(np, q);
+    return o;
+}
+__host__ __device__ constexpr int fft_tw_size(int np) { return fft_tw_offset(np, fft_npasses(np)); }
+
+// padded shared-memory index: one spare complex per 16 keeps strided pass writes conflict-free
+__device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
+__host__ __device__ constexpr int xpad_len(int n) { return n + (n >> 4); }
+
+// Butterflies of pass P: thread j handles butterflies b = j + (NP/16) s, s in [0, 16/R); element r
+// of butterfly s lives in slot s + r (16/R).
+template <int NP, int P, bool INV>
+__device__ __forceinline__ void fft_pass(float2 (&x)[16], const int j,
+                                         const float2* __restrict__ tw) {
+    constexpr int R = fft_radix(NP, P), NS = fft_ns(NP, P), S = 16 / R;
+    constexpr int TW = fft_tw_offset(NP, P);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        if constexpr (P > 0) {
+            const int a = (j + (NP / 16) * s) & (NS - 1);
+#pragma unroll
+            for (int r = 1; r < R; ++r)
+                x[s + r * S] = c_tw<INV>(x[s + r * S], __ldg(tw + TW + (r - 1) * NS + a));
+        }
+        dft_slots<R, S, INV>(x, s);
+    }
+}
+
+// Exchange arrays interleave the two polarizations: element n of polarization p is at
+// e[2 xpad(n) + p], so the x/y partner threads (adjacent lanes) touch adjacent words.
+template <int NP, int P>
+__device__ __forceinline__ void fft_store(float2* e, const float2 (&x)[16], const int j) {
+    constexpr int R = fft_radix(NP, P), NS = fft_ns(NP, P), S = 16 / R;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int b = j + (NP / 16) * s;
+        const int base = (b / NS) * NS * R + (b & (NS - 1));
+#pragma unroll
+        for (int q = 0; q < R; ++q) e[2 * xpad(base + q * NS)] = x[s + q * S];
+    }
+}
+
+template <int NP, int P>
+__device__ __forceinline__ void fft_load(const float2* e, float2 (&x)[16], const int j) {
+    constexpr int R = fft_radix(NP, P), S = 16 / R;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+        const int b = j + (NP / 16) * s;
+#pragma unroll
+        for (int r = 0; r < R; ++r) x[s + r * S] = e[2 * xpad(b + r * (NP / R))];
+    }
+}
+
+// Unnormalized DFT of size NP of one polarization held by the NP/16 threads of one group.
+// INV = false: X[k] = sum_n x[n] exp(-j 2 pi k n / NP);  INV = true: exp(+j ...).
+// `bar` synchronizes the group (both polarizations); `e` is this thread's polarization view of
+// the group's interleaved exchange array (base + p).
+template <int NP, bool INV, class Bar>
+__device__ __forceinline__ void fft_regs(float2 (&x)[16], const int j, float2* e,
+                                         const float2* __restrict__ tw, Bar bar) {
+    constexpr int NPASS = fft_npasses(NP);
+    fft_pass<NP, 0, INV>(x, j, tw);
+    if constexpr (NPASS > 1) {
+        bar();
+        fft_store<NP, 0>(e, x, j);
+        bar();
+        fft_load<NP, 1>(e, x, j);
+        fft_pass<NP, 1, INV>(x, j, tw);
+    }
+    if constexpr (NPASS > 2) {
+        bar();
+        fft_store<NP, 1>(e, x, j);
+        bar();
+        fft_load<NP, 2>(e, x, j);
+        fft_pass<NP, 2, INV>(x, j, tw);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// mbarrier + bulk copy (TMA, non-tensor form) with bounded waits
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// Wait for phase `parity` of `bar`, giving up after roughly `max_cycles` SM cycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long max_cycles) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > max_cycles) return false;
+    }
+    return true;
+}
+// global -> shared bulk copy completing on `bar` (addresses 16-byte aligned, bytes % 16 == 0)
+__device__ __forceinline__ void bulk_copy_g2s(void* dst_smem, const void* src_gmem, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst_smem)), "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+// order earlier generic-proxy shared-memory accesses before later async-proxy (TMA) ones
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// named barrier over `count` threads (a multiple of 32)
+__device__ __forceinline__ void named_bar(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// device status bits
+constexpr unsigned int kStatusTimeout = 1u;
+
+}  // namespace cbessfm

@@ -1,0 +1,58 @@
+// internal.h -- host-side plan layout and kernel launch interfaces (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/cbessfm.h"
+
+namespace cbessfm {
+
+// Kernel arguments of the chain kernels (forward and adjoint share them).
+struct ChainArgs {
+    const void* in;              // [batch][L] samples (storage type of the plan)
+    void* out;                   // [batch][L]
+    long long L;                 // samples per sequence
+    int batch;
+    int n_sb, n_st;              // subbands, steps
+    int N, n_ov, V, n_blocks;    // block size, total overlap, valid samples, blocks per sequence
+    int G;                       // OLS blocks per CTA
+    int nc, ntaps_pad, nchunks;  // FIR: N_c, taps per row (multiple of 4), chunks of 4 taps
+    int H, p_off, pstride;       // FIR intensity buffer: halo, alignment offset, row stride
+    int region_bytes;            // shared memory per OLS block
+    const float2* gvd;           // [3][n_sb][NP]: first (x 1/N), interior (x 1/NP), last (x 1/NP)
+    const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
+    const float2* fft_tw;        // FFT pass twiddles (fft_tw_size(NP))
+    const float* taps;           // [n_st][n_sb][n_sb][ntaps_pad]
+    unsigned int* status;        // device status word
+};
+
+struct PlanImpl {
+    int device = 0;
+    cbessfm_link link{};
+    int n_sb = 1, n_st = 0, ntaps = 1, n_fft = 16, overlap = 0;
+    double ratio = 0.5;
+    cbessfm_storage storage = CBESSFM_C64;
+    int N = 16, n_ov = 0, V = 16;
+    int nc = 0, ntaps_pad = 4, nchunks = 1, H = 4, p_off = 3, pstride = 32;
+    int region_bytes = 0, G = 1, threads = 0;
+    double step_length = 0.0;
+    float2* d_gvd = nullptr;      // [3][n_sb][NP]
+    float* d_kdisp = nullptr;     // [n_sb][NP] 2 pi^2 beta2 L_step f^2 (ratio derivative)
+    float2* d_mix_tw = nullptr;   // [n_sb][N]
+    float2* d_fft_tw = nullptr;
+    float* d_taps = nullptr;      // [n_st][n_sb][n_sb][ntaps_pad]
+    unsigned int* d_status = nullptr;
+};
+
+// FP64 kernel that fills the three GVD tables (and the ratio-derivative table) on `stream`.
+cudaError_t launch_build_gvd(const PlanImpl& p, cudaStream_t stream);
+
+// Forward chain kernel; returns cudaSuccess or the launch error.
+cudaError_t launch_forward(const PlanImpl& p, const ChainArgs& a, cudaStream_t stream);
+// Maximum dynamic shared memory of the forward kernel instantiation for this NP (opt-in limit).
+cudaError_t prepare_forward(int np, int smem_bytes);
+
+ChainArgs make_chain_args(const PlanImpl& p);
+
+}  // namespace cbessfm

@@ -1,0 +1,71 @@
+"""Helpers shared by the GPU parity tests: one case description feeds both the CUDA plan and the
+FP64 oracle with identical parameters and inputs."""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from oracle import dbp as odbp
+from synth import signals
+
+
+@dataclass
+class Case:
+    n_sb: int
+    n_fft: int
+    overlap: int
+    n_st: int
+    ntaps: int
+    ratio: float
+    L: int
+    batch: int = 1
+    beta2: float = -21.7e-27
+    span_length: float = 80e3
+    n_spans: int = 1
+    sample_rate: float = 64e9
+    tap_scale: float = 0.1
+    field_scale: float = 1.0
+    seed: int = 0
+
+    @property
+    def link_length(self) -> float:
+        return self.span_length * self.n_spans
+
+
+def random_field(case: Case) -> np.ndarray:
+    rng = np.random.default_rng(case.seed)
+    shape = (case.batch, case.L, 2)
+    f = (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2)
+    return (case.field_scale * f).astype(np.complex128)
+
+
+def case_taps(case: Case) -> np.ndarray:
+    return signals.random_taps(case.seed + 17, case.n_st, case.n_sb, case.ntaps, case.tap_scale,
+                               spread=0.3)
+
+
+def oracle_params(case: Case, taps: np.ndarray) -> odbp.ChainParams:
+    return odbp.ChainParams(beta2=case.beta2, sample_rate=case.sample_rate,
+                            link_length=case.link_length, n_sb=case.n_sb, ratio=case.ratio,
+                            taps=np.asarray(taps, dtype=np.float64))
+
+
+def make_plan(case: Case, taps: np.ndarray):
+    from paper_2409_14489_gb300 import cbessfm
+    link = cbessfm.make_link(case.beta2, case.span_length, case.n_spans, case.sample_rate)
+    return cbessfm.Plan(link, case.n_sb, case.n_st, case.ratio,
+                        np.asarray(taps, dtype=np.float32), case.n_fft, case.overlap)
+
+
+def run_gpu(plan, field: np.ndarray) -> np.ndarray:
+    import torch
+    x = torch.from_numpy(np.ascontiguousarray(field.astype(np.complex64))).cuda()
+    y = plan.backpropagate(x)
+    torch.cuda.synchronize()
+    return y.cpu().numpy().astype(np.complex128)
+
+
+def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))

@@ -1,0 +1,70 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, exports every function the
+header declares, and rejects invalid arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "cbessfm.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cbessfm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2409_14489_gb300 import cbessfm
+    return cbessfm
+
+
+def test_library_exports_every_declared_function(lib):
+    names = _declared_functions()
+    assert "cbessfm_backpropagate" in names and "cbessfm_plan_create" in names
+    so = ctypes.CDLL(lib._LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_version_string(lib):
+    assert "sm_103a" in lib.version()
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(bands=0), "bands"), (dict(bands=17), "bands"), (dict(steps=-1), "steps"),
+    (dict(ratio=1.5), "ratio"), (dict(ratio=-0.1), "ratio"), (dict(n_fft=100), "n_fft"),
+    (dict(n_fft=8), "n_fft"), (dict(n_fft=4096), "n_fft"), (dict(ntaps=4), "ntaps"),
+    (dict(ntaps=129), "ntaps"), (dict(overlap=3), "overlap"), (dict(overlap=256), "overlap"),
+])
+def test_plan_create_rejects_invalid_arguments(lib, kw, msg):
+    import numpy as np
+    args = dict(bands=1, steps=1, ratio=0.5, ntaps=5, n_fft=256, overlap=64)
+    args.update(kw)
+    taps = np.zeros((max(args["steps"], 0), max(args["bands"], 0), max(args["bands"], 0),
+                     args["ntaps"]), np.float32)
+    link = lib.make_link(-21.7e-27, 80e3, 1, 64e9)
+    h = ctypes.c_void_p()
+    st = lib.lib().cbessfm_plan_create(
+        ctypes.byref(link), args["bands"], args["steps"], args["ratio"],
+        taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if taps.size else None,
+        args["ntaps"], args["n_fft"], args["overlap"], 0, ctypes.byref(h))
+    assert st == lib.ERR_INVALID_ARG
+    assert msg in lib.lib().cbessfm_last_error().decode()
+    assert not h.value
+
+
+def test_invalid_link_and_null_arguments(lib):
+    link = lib.make_link(-21.7e-27, 80e3, 1, 0.0)
+    h = ctypes.c_void_p()
+    assert lib.lib().cbessfm_plan_create(ctypes.byref(link), 1, 0, 0.5, None, 1, 64, 16, 0,
+                                         ctypes.byref(h)) == lib.ERR_INVALID_ARG
+    assert lib.lib().cbessfm_plan_create(None, 1, 0, 0.5, None, 1, 64, 16, 0,
+                                         ctypes.byref(h)) == lib.ERR_INVALID_ARG
+    assert lib.lib().cbessfm_backpropagate(None, None, None, 10, 1, None) == lib.ERR_INVALID_ARG
+    assert lib.lib().cbessfm_plan_destroy(None) == lib.OK
