@@ -31,7 +31,7 @@ SMALL_CASES = [
     Case(4, 512, 128, 3, 9, 1.0, 2 * 1536 + 300, sample_rate=256e9),
     Case(5, 1024, 256, 2, 11, 0.3, 2 * 3840 + 1001, sample_rate=640e9),
     Case(2, 2048, 512, 2, 11, 0.0, 2 * 3072 + 77, sample_rate=128e9),
-    Case(5, 2048, 512, 1, 11, 0.3, 10240 + 4000, sample_rate=640e9),
+    Case(2, 2048, 512, 1, 11, 0.3, 4096 + 4000, sample_rate=256e9, seed=4),
     Case(3, 32, 8, 0, 1, 0.5, 200, sample_rate=96e9),             # EDC (no NLPR steps)
     Case(2, 64, 16, 4, 1, 0.5, 333, sample_rate=128e9),           # single-tap (OSSFM-like)
     Case(1, 64, 0, 2, 5, 0.5, 64 * 3),                            # no overlap
