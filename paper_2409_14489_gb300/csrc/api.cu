@@ -37,7 +37,7 @@ cbessfm_status cuda_fail(cudaError_t e, const char* what) {
                 cudaGetErrorString(e));
 }
 
-constexpr int kMaxDynSmem = 226 * 1024;     // 227 KB opt-in minus room for static shared memory
+constexpr int kMaxDynSmem = 224 * 1024;     // 227 KB per block minus room for static shared memory
 constexpr int kMaxThreads = 640;
 constexpr int kMaxG = 16;
 
@@ -51,12 +51,14 @@ void free_plan(PlanImpl& p) {
     cudaFree(p.d_mix_tw);
     cudaFree(p.d_fft_tw);
     cudaFree(p.d_taps);
+    cudaFree(p.d_rot);
     cudaFree(p.d_status);
     p.d_gvd = nullptr;
     p.d_kdisp = nullptr;
     p.d_mix_tw = nullptr;
     p.d_fft_tw = nullptr;
     p.d_taps = nullptr;
+    p.d_rot = nullptr;
     p.d_status = nullptr;
 }
 
@@ -86,10 +88,13 @@ ChainArgs make_chain_args(const PlanImpl& p) {
     a.p_off = p.p_off;
     a.pstride = p.pstride;
     a.region_bytes = p.region_bytes;
+    a.nlpr_off = p.nlpr_off;
+    a.sep = p.sep;
     a.gvd = p.d_gvd;
     a.mix_tw = p.d_mix_tw;
     a.fft_tw = p.d_fft_tw;
     a.taps = p.d_taps;
+    a.rot_tbl = p.d_rot;
     a.status = p.d_status;
     return a;
 }
@@ -147,7 +152,7 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     p.ntaps_pad = 4 * p.nchunks;
     p.H = round_up(p.nc + 4, 4);
     p.p_off = ((3 - p.nc) % 4 + 4) % 4;
-    p.pstride = n_fft + 2 * p.H + 8;
+    p.pstride = round_up(n_fft + 2 * p.H + 8, 32);   // rows start on 128-byte boundaries
 
     const int tpf = n_fft / 16;
     const int tb = 2 * bands * tpf;                 // one polarization per thread
@@ -156,8 +161,17 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
                     kMaxThreads);
     const int need_stage = 16 * p.N;
     const int need_exch = 16 * xpad_len(p.N);
-    const int need_fir = 4 * bands * p.pstride + 8 * bands * n_fft;   // P rows + (cos, sin)
-    p.region_bytes = round_up(std::max(need_stage, std::max(need_exch, need_fir)), 128);
+    const int need_nlpr = 4 * bands * p.pstride + 8 * bands * xpad_len(n_fft);  // P + (cos, sin)
+    const int base = round_up(std::max(need_stage, need_exch), 128);
+    if (base + round_up(need_nlpr, 128) <= kMaxDynSmem) {
+        p.sep = 1;                                    // separate rows: fewer barriers per step
+        p.nlpr_off = base;
+        p.region_bytes = base + round_up(need_nlpr, 128);
+    } else {
+        p.sep = 0;
+        p.nlpr_off = 0;
+        p.region_bytes = round_up(std::max(base, need_nlpr), 128);
+    }
     if (p.region_bytes > kMaxDynSmem)
         return fail(CBESSFM_ERR_UNSUPPORTED, "block of %d samples needs %d B of shared memory",
                     p.N, p.region_bytes);
@@ -199,6 +213,12 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
             mix_tw[(size_t)r * p.N + K] = make_float2((float)std::cos(ang), (float)std::sin(ang));
         }
 
+    std::vector<float2> rot(256);
+    for (int k = 0; k < 256; ++k) {
+        const double ang = two_pi * k / 256.0;
+        rot[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+
     const size_t n_taps_dev = std::max<size_t>(1, (size_t)steps * bands * bands * p.ntaps_pad);
 #define CB_TRY(call, what)                    \
     do {                                      \
@@ -214,6 +234,9 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     CB_TRY(cudaMalloc(&p.d_fft_tw, sizeof(float2) * fft_tw.size()), "cudaMalloc(fft tw)");
     CB_TRY(cudaMalloc(&p.d_taps, sizeof(float) * n_taps_dev), "cudaMalloc(taps)");
     CB_TRY(cudaMalloc(&p.d_status, sizeof(unsigned int)), "cudaMalloc(status)");
+    CB_TRY(cudaMalloc(&p.d_rot, sizeof(float2) * rot.size()), "cudaMalloc(rot)");
+    CB_TRY(cudaMemcpy(p.d_rot, rot.data(), sizeof(float2) * rot.size(), cudaMemcpyHostToDevice),
+           "copy rotation table");
     CB_TRY(cudaMemset(p.d_status, 0, sizeof(unsigned int)), "cudaMemset(status)");
     CB_TRY(cudaMemcpy(p.d_fft_tw, fft_tw.data(), sizeof(float2) * fft_tw.size(),
                       cudaMemcpyHostToDevice), "copy fft twiddles");

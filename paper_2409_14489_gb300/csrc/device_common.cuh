@@ -194,26 +194,53 @@ __device__ __forceinline__ void fft_pass(float2 (&x)[16], const int j,
 
 // Exchange arrays interleave the two polarizations: element n of polarization p is at
 // e[2 xpad(n) + p], so the x/y partner threads (adjacent lanes) touch adjacent words.
+// For NP >= 256 every element index of a pass is f(j) + c with c a compile-time multiple of 16,
+// so xpad(f(j) + c) = xpad(f(j)) + c + c/16 and each access is one base register plus an
+// immediate offset.
 template <int NP, int P>
 __device__ __forceinline__ void fft_store(float2* e, const float2 (&x)[16], const int j) {
     constexpr int R = fft_radix(NP, P), NS = fft_ns(NP, P), S = 16 / R;
+    if constexpr (NP >= 256) {
+        // b = j + (NP/16) s;  n = (b / NS) NS R + (b mod NS) + q NS
+        const int f = (j / NS) * NS * R + (j & (NS - 1));
+        float2* eb = e + 2 * xpad(f);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const int b = j + (NP / 16) * s;
-        const int base = (b / NS) * NS * R + (b & (NS - 1));
+        for (int s = 0; s < S; ++s)
 #pragma unroll
-        for (int q = 0; q < R; ++q) e[2 * xpad(base + q * NS)] = x[s + q * S];
+            for (int q = 0; q < R; ++q) {
+                const int c = ((NP / 16) * s / NS) * NS * R + q * NS;   // multiple of 16
+                eb[2 * (c + c / 16)] = x[s + q * S];
+            }
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int b = j + (NP / 16) * s;
+            const int base = (b / NS) * NS * R + (b & (NS - 1));
+#pragma unroll
+            for (int q = 0; q < R; ++q) e[2 * xpad(base + q * NS)] = x[s + q * S];
+        }
     }
 }
 
 template <int NP, int P>
 __device__ __forceinline__ void fft_load(const float2* e, float2 (&x)[16], const int j) {
     constexpr int R = fft_radix(NP, P), S = 16 / R;
+    if constexpr (NP >= 256) {
+        const float2* eb = e + 2 * xpad(j);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-        const int b = j + (NP / 16) * s;
+        for (int s = 0; s < S; ++s)
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[s + r * S] = e[2 * xpad(b + r * (NP / R))];
+            for (int r = 0; r < R; ++r) {
+                const int c = (NP / 16) * s + r * (NP / R);              // multiple of 16
+                x[s + r * S] = eb[2 * (c + c / 16)];
+            }
+    } else {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            const int b = j + (NP / 16) * s;
+#pragma unroll
+            for (int r = 0; r < R; ++r) x[s + r * S] = e[2 * xpad(b + r * (NP / R))];
+        }
     }
 }
 

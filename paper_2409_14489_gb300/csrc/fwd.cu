@@ -20,7 +20,25 @@
 namespace cbessfm {
 
 constexpr int kMaxG = 16;
-constexpr float kInvPi = 0.318309886183790671538f;
+// exp(j theta) by table look-up (the paper computes the exponential with a LUT): theta =
+// 2 pi k / 256 + d with |d| <= pi / 256; the table entry is built in FP64 by the plan and the
+// residual rotation is 1 - d^2/2 + j d (1 - d^2/6), whose truncation error (< 1e-9) is far below
+// float rounding.  d comes from a two-constant Cody-Waite reduction: the step 2 pi / 256 =
+// kRotStepHi + kRotStepLo with kRotStepHi exact in 8 bits, so k * kRotStepHi is exact for
+// |k| < 2^16 (|theta| < 1600 rad).
+constexpr int kRotTable = 256;
+constexpr float kRotInvStep = 40.7436654315252059568f;     // 256 / (2 pi)
+constexpr float kRotStepHi = 0.0245361328125f;              // 201 / 8192
+constexpr float kRotStepLo = 7.5597936702587190e-6f;        // 2 pi / 256 - 201 / 8192
+
+__device__ __forceinline__ float2 rotation_factor(float th, const float2* __restrict__ tbl) {
+    const float kf = rintf(th * kRotInvStep);
+    float d = fmaf(-kf, kRotStepHi, th);
+    d = fmaf(-kf, kRotStepLo, d);
+    const float2 t = tbl[(int)kf & (kRotTable - 1)];
+    const float d2 = d * d;
+    return c_mul(t, make_float2(fmaf(-0.5f, d2, 1.0f), d * fmaf(-0.16666666666666667f, d2, 1.0f)));
+}
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: never reached by a live copy
 
 // Barrier over the 2 NP/16 threads (both polarizations) of one FFT group.  Groups of a warp or
@@ -37,27 +55,38 @@ struct GroupBar {
     }
 };
 
-// Phase of the nonlinear rotation for the 8 samples k = k0 .. k0 + 7 of subband i, step s:
+// Intensity rows are XOR-swizzled in 16-byte granules: float m of a row lives at
+// m ^ (((m >> 5) & 1) << 2).  The FIR's lanes read float4 windows 32 bytes apart; the swizzle
+// puts the two 32-float halves of every 8-lane group on complementary banks.
+__device__ __forceinline__ int pswz(int m) { return m ^ (((m >> 5) & 1) << 2); }
+// (cos, sin) rows carry one spare float2 per 16 so the 8-sample runs of adjacent lanes do not
+// collide on a bank.
+__device__ __forceinline__ int cpad(int k) { return k + (k >> 4); }
+
+// Rotation factors for the 8 samples k = k0 .. k0 + 7 of subband i, step s:
 // theta_i[k] = sum_l sum_m w[s][i][l][m + nc] P_l[k - m]; stores (cos theta, sin theta).
 // P rows carry a circular halo of H samples on each side, so no index wraps here; each chunk of
 // four taps reads a 12-sample window with aligned 16-byte loads.
-__device__ __forceinline__ void nlpr_phase8(const ChainArgs& a, const float* __restrict__ pbase,
-                                            float2* __restrict__ cs_row, int s, int i, int k0) {
+__device__ __forceinline__ void nlpr_rotation8(const ChainArgs& a, const float* __restrict__ prow0,
+                                               float2* __restrict__ cs_row,
+                                               const float2* __restrict__ rot_tbl, int s, int i,
+                                               int k0) {
     const float4* wbase = reinterpret_cast<const float4*>(
         a.taps + (size_t)(s * a.n_sb + i) * a.n_sb * a.ntaps_pad);
     float acc[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+    const int m0 = a.H + a.p_off + k0 + a.nc - 3;      // row index of the first window sample
     for (int l = 0; l < a.n_sb; ++l) {
-        const float* pl = pbase + l * a.pstride + a.H + a.p_off + k0 + a.nc - 3;
+        const float* pl = prow0 + l * a.pstride;
         const float4* wrow = wbase + l * a.nchunks;
         for (int c = 0; c < a.nchunks; ++c) {
             const float4 w4 = __ldg(wrow + c);
-            const float4* src = reinterpret_cast<const float4*>(pl - 4 * c);
+            const int m = m0 - 4 * c;
             float win[12];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
-                const float4 v = src[e];
+                const float4 v = *reinterpret_cast<const float4*>(pl + pswz(m + 4 * e));
                 win[4 * e] = v.x; win[4 * e + 1] = v.y; win[4 * e + 2] = v.z; win[4 * e + 3] = v.w;
             }
 #pragma unroll
@@ -71,12 +100,9 @@ __device__ __forceinline__ void nlpr_phase8(const ChainArgs& a, const float* __r
             }
         }
     }
+    float2* dst = cs_row + cpad(k0);                   // k0 % 16 in {0, 8}: no carry below
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        float sn, cs;
-        sincospif(acc[q] * kInvPi, &sn, &cs);          // exact argument reduction, no slow path
-        cs_row[k0 + q] = make_float2(cs, sn);
-    }
+    for (int q = 0; q < 8; ++q) dst[q] = rotation_factor(acc[q], rot_tbl);
 }
 
 // Thread layout of one OLS block (TB = 2 n_sb NP/16 threads): rem = 2 jj + p with p the
@@ -87,8 +113,10 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
     constexpr int XL = 2 * xpad_len(NP);               // float2 per group exchange array
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kMaxG];
+    __shared__ float2 s_rot[kRotTable];
 
     const int tid = threadIdx.x;
+    for (int k = tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
     const int TB = 2 * a.n_sb * TPF;
     const int g = tid / TB;
     const int rem = tid - g * TB;
@@ -176,34 +204,42 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
 #pragma unroll
         for (int t = 0; t < 16; ++t) x[t] = c_mul(x[t], __ldg(h + j + TPF * t));
     }
-    float* pbase = reinterpret_cast<float*>(region);
-    float2* csbase = reinterpret_cast<float2*>(pbase + a.n_sb * a.pstride);
-    const float2* cs_mine = csbase + gi * NP;
+    // intensity rows and (cos, sin) rows: after the exchange arrays when they fit (a.sep), else
+    // aliased onto them (then two more block-wide barriers per step guard the reuse)
+    float* prow0 = reinterpret_cast<float*>(region + a.nlpr_off);
+    float2* csbase = reinterpret_cast<float2*>(prow0 + a.n_sb * a.pstride);
+    const float2* cs_mine = csbase + gi * (NP + NP / 16);
+    const int cs_base = (NP >= 256) ? cpad(j) : 0;
 #pragma unroll 1
     for (int s = 0; s < a.n_st; ++s) {
         fft_regs<NP, true>(x, j, e, a.fft_tw, bar);               // subband time samples
-        __syncthreads();
+        if (!a.sep) __syncthreads();
         {
-            float* prow = pbase + gi * a.pstride + a.H + a.p_off;
+            float* prow = prow0 + gi * a.pstride;
+            const int mb = a.H + a.p_off;
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
                 float pw = fmaf(x[t].x, x[t].x, x[t].y * x[t].y);
                 pw += __shfl_xor_sync(0xffffffffu, pw, 1);          // |x|^2 + |y|^2
                 if (p == 0) {
                     const int n = j + TPF * t;
-                    prow[n] = pw;
+                    prow[pswz(mb + n)] = pw;
                     // circular halo: H <= NP (ntaps <= NP/2), so one copy per side suffices
-                    if (n < a.H) prow[n + NP] = pw;
-                    if (n >= NP - a.H) prow[n - NP] = pw;
+                    if (n < a.H) prow[pswz(mb + n + NP)] = pw;
+                    if (n >= NP - a.H) prow[pswz(mb + n - NP)] = pw;
                 }
             }
         }
         __syncthreads();
-        nlpr_phase8(a, pbase, csbase + gi * NP, s, gi, 16 * j + 8 * p);
+        nlpr_rotation8(a, prow0, csbase + gi * (NP + NP / 16), s_rot, s, gi, 16 * j + 8 * p);
         __syncthreads();
 #pragma unroll
-        for (int t = 0; t < 16; ++t) x[t] = c_mul(x[t], cs_mine[j + TPF * t]);
-        __syncthreads();
+        for (int t = 0; t < 16; ++t) {
+            const float2 rot = (NP >= 256) ? cs_mine[cs_base + (TPF + TPF / 16) * t]
+                                           : cs_mine[cpad(j + TPF * t)];
+            x[t] = c_mul(x[t], rot);
+        }
+        if (!a.sep) __syncthreads();
         fft_regs<NP, false>(x, j, e, a.fft_tw, bar);              // back to subband bins
         const float2* h = a.gvd + (size_t)((s < a.n_st - 1 ? 1 : 2) * a.n_sb + gi) * NP;
 #pragma unroll

@@ -20,10 +20,13 @@ struct ChainArgs {
     int nc, ntaps_pad, nchunks;  // FIR: N_c, taps per row (multiple of 4), chunks of 4 taps
     int H, p_off, pstride;       // FIR intensity buffer: halo, alignment offset, row stride
     int region_bytes;            // shared memory per OLS block
+    int nlpr_off;                // byte offset of the intensity / (cos, sin) rows in the region
+    int sep;                     // 1 if those rows do not alias the exchange arrays
     const float2* gvd;           // [3][n_sb][NP]: first (x 1/N), interior (x 1/NP), last (x 1/NP)
     const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
     const float2* fft_tw;        // FFT pass twiddles (fft_tw_size(NP))
     const float* taps;           // [n_st][n_sb][n_sb][ntaps_pad]
+    const float2* rot_tbl;       // [256] exp(j 2 pi k / 256)
     unsigned int* status;        // device status word
 };
 
@@ -35,13 +38,14 @@ struct PlanImpl {
     cbessfm_storage storage = CBESSFM_C64;
     int N = 16, n_ov = 0, V = 16;
     int nc = 0, ntaps_pad = 4, nchunks = 1, H = 4, p_off = 3, pstride = 32;
-    int region_bytes = 0, G = 1, threads = 0;
+    int region_bytes = 0, nlpr_off = 0, sep = 0, G = 1, threads = 0;
     double step_length = 0.0;
     float2* d_gvd = nullptr;      // [3][n_sb][NP]
     float* d_kdisp = nullptr;     // [n_sb][NP] 2 pi^2 beta2 L_step f^2 (ratio derivative)
     float2* d_mix_tw = nullptr;   // [n_sb][N]
     float2* d_fft_tw = nullptr;
     float* d_taps = nullptr;      // [n_st][n_sb][n_sb][ntaps_pad]
+    float2* d_rot = nullptr;      // [256] exp(j 2 pi k / 256) from FP64
     unsigned int* d_status = nullptr;
 };
 

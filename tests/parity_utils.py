@@ -2,7 +2,9 @@
 FP64 oracle with identical parameters and inputs."""
 from __future__ import annotations
 
+import json
 import math
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -67,5 +69,11 @@ def run_gpu(plan, field: np.ndarray) -> np.ndarray:
     return y.cpu().numpy().astype(np.complex128)
 
 
-def rel_l2(a: np.ndarray, b: np.ndarray) -> float:
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+def rel_l2(a: np.ndarray, b: np.ndarray, name: str = "") -> float:
+    """Relative L2 error ||a - b|| / ||b||; logged to $CBESSFM_PARITY_LOG (JSON lines) if set."""
+    err = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    log = os.environ.get("CBESSFM_PARITY_LOG")
+    if log and name:
+        with open(log, "a") as f:
+            f.write(json.dumps({"case": name, "rel_l2": err}) + "\n")
+    return err

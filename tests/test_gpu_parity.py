@@ -51,7 +51,8 @@ def test_forward_matches_oracle_small(case):
     for b in range(case.batch):
         want = odbp.dbp_mode_b(field[b].astype(np.complex64).astype(np.complex128), p,
                                case.n_fft, case.overlap)
-        assert rel_l2(got[b], want) <= TOL, (b, rel_l2(got[b], want))
+        err = rel_l2(got[b], want, f"small/{case}/b{b}")
+        assert err <= TOL, (b, err)
     assert plan.status() == 0
 
 
@@ -72,7 +73,7 @@ def test_c1_channel_output_parity_and_snr():
     got = run_gpu(plan, rx32[None])[0]
     want = odbp.dbp_mode_b(rx32.astype(np.complex128), oracle_params(
         case, taps.astype(np.float32).astype(np.float64)), d.n_fft, d.overlap)
-    assert rel_l2(got, want) <= TOL
+    assert rel_l2(got, want, "c1_channel") <= TOL
     p_pol = p_w / 2
     snr_gpu = evaluate.snr_db(evaluate.receive(got, sig.sample_rate, sig.baud, sig.rolloff, 0.0,
                                                p_pol), syms[0])
@@ -111,7 +112,8 @@ def test_c2_full_size_sampled_blocks():
         blocks = sorted({0, n_blocks - 1, int(rng.integers(1, n_blocks - 1))})
         want = odbp.dbp_mode_b(f32[b].astype(np.complex128), p, d.n_fft, d.overlap, blocks=blocks)
         sel = ~np.isnan(want[:, 0])
-        assert rel_l2(got[b][sel], want[sel]) <= TOL, (b, blocks)
+        err = rel_l2(got[b][sel], want[sel], f"c2_full/realization{b}")
+        assert err <= TOL, (b, blocks, err)
     assert np.isfinite(got).all()
 
 
