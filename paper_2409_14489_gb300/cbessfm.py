@@ -133,19 +133,28 @@ class Plan:
     def n_blocks(self, n_samples: int) -> int:
         return -(-n_samples // self.valid)
 
-    def backpropagate(self, x, out=None, stream=None):
-        """Run DBP on a complex64 CUDA tensor of shape (L, 2) or (batch, L, 2)."""
+    def _field_dtype(self):
         import torch
-        if not (x.is_cuda and x.dtype == torch.complex64 and x.is_contiguous()):
-            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        return {STORAGE_C64: torch.complex64, STORAGE_F16X4: torch.float16,
+                STORAGE_BF16X4: torch.bfloat16}[self.storage]
+
+    def backpropagate(self, x, out=None, stream=None):
+        """Run DBP on a contiguous CUDA tensor in the plan's storage: complex64 of shape (L, 2) or
+        (batch, L, 2); for fp16/bf16 storage, float16/bfloat16 of shape (L, 4) or (batch, L, 4)
+        holding (x.re, x.im, y.re, y.im)."""
+        import torch
+        want = self._field_dtype()
+        last = 2 if self.storage == STORAGE_C64 else 4
+        if not (x.is_cuda and x.dtype == want and x.is_contiguous()):
+            raise ValueError(f"x must be a contiguous {want} CUDA tensor")
         if x.dim() == 2:
             batch, L = 1, x.shape[0]
         elif x.dim() == 3:
             batch, L = x.shape[0], x.shape[1]
         else:
-            raise ValueError("x must have shape (L, 2) or (batch, L, 2)")
-        if x.shape[-1] != 2:
-            raise ValueError("last dimension must be the two polarizations")
+            raise ValueError(f"x must have shape (L, {last}) or (batch, L, {last})")
+        if x.shape[-1] != last:
+            raise ValueError(f"last dimension must be {last}")
         if out is None:
             out = torch.empty_like(x)
         _check(_lib.cbessfm_backpropagate(self._h, x.data_ptr(), out.data_ptr(), L, batch,

@@ -131,8 +131,8 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     if (overlap < 0 || (overlap & 1) || overlap >= n_fft)
         return fail(CBESSFM_ERR_INVALID_ARG, "overlap must be even and in [0, n_fft)");
     if (steps > 0 && coeffs == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "coeffs is NULL");
-    if (storage != CBESSFM_C64)
-        return fail(CBESSFM_ERR_NOT_IMPLEMENTED, "only complex64 storage is built");
+    if (storage != CBESSFM_C64 && storage != CBESSFM_F16x4 && storage != CBESSFM_BF16x4)
+        return fail(CBESSFM_ERR_INVALID_ARG, "unknown storage type");
 
     PlanImpl p;
     p.link = *link;
@@ -154,11 +154,10 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     p.p_off = ((3 - p.nc) % 4 + 4) % 4;
     p.pstride = round_up(n_fft + 2 * p.H + 8, 32);   // rows start on 128-byte boundaries
 
-    const int tpf = n_fft / 16;
+    const int tpf = n_fft / fft_slots(n_fft);
     const int tb = 2 * bands * tpf;                 // one polarization per thread
     if (tb > kMaxThreads)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "bands * n_fft / 16 = %d threads exceeds %d", tb,
-                    kMaxThreads);
+        return fail(CBESSFM_ERR_UNSUPPORTED, "%d threads per block exceed %d", tb, kMaxThreads);
     const int need_stage = 16 * p.N;
     const int need_exch = 16 * xpad_len(p.N);
     const int need_nlpr = 4 * bands * p.pstride + 8 * bands * xpad_len(n_fft);  // P + (cos, sin)
@@ -249,7 +248,7 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
                           cudaMemcpyHostToDevice), "copy taps");
     }
     CB_TRY(launch_build_gvd(p, nullptr), "build GVD tables");
-    CB_TRY(prepare_forward(n_fft, kMaxDynSmem), "set shared-memory limit");
+    CB_TRY(prepare_forward(n_fft, (int)storage, kMaxDynSmem), "set shared-memory limit");
     CB_TRY(cudaDeviceSynchronize(), "plan tables");
 #undef CB_TRY
 
@@ -313,10 +312,11 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
     if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
     if (n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples must be >= 1");
     if (batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "batch must be >= 1");
+    const PlanImpl& p = plan->impl;
+    const unsigned long long sample_bytes = p.storage == CBESSFM_C64 ? 16ull : 8ull;
     if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u)
         return fail(CBESSFM_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
-    const PlanImpl& p = plan->impl;
-    const unsigned long long bytes = (unsigned long long)n_samples * batch * 16ull;
+    const unsigned long long bytes = (unsigned long long)n_samples * batch * sample_bytes;
     const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
     if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
     const long long n_blocks = (n_samples + p.V - 1) / p.V;

@@ -2,13 +2,13 @@
 //
 //  * complex float2 arithmetic,
 //  * radix-2/4/8/16 DFT butterflies on register slots,
-//  * a Stockham FFT of size NP (16..2048) executed by NP/16 threads that each own 16 register
-//    slots of one polarization, exchanging through padded shared memory between passes (the
-//    x and y threads of the same slots sit in adjacent lanes and share the exchange array),
+//  * a Stockham FFT of size NP (16..2048) executed by NP/E threads that each own E (16 or 32)
+//    register slots of one polarization, exchanging through padded shared memory between passes
+//    (the x and y threads of the same slots sit in adjacent lanes and share the exchange array),
 //  * mbarrier + bulk-copy (TMA) helpers with bounded waits.
 //
 // Slot convention (shared by the forward and adjoint kernels): thread j of an FFT group holds,
-// in slot t (0..15), element j + (NP/16) * t of the sequence, both on the time side and on the
+// in slot t (0..E-1), element j + (NP/E) * t of the sequence, both on the time side and on the
 // frequency side.  The Stockham passes are arranged (radix 16 first and last) so that the first
 // pass reads exactly these elements and the last pass produces exactly these elements; the
 // pointwise steps (dispersion, rotation) therefore run on registers with no reordering.
@@ -130,11 +130,20 @@ __device__ __forceinline__ void dft16(float2 (&v)[16]) {
     for (int k = 0; k < 16; ++k) v[k] = x[k];
 }
 
-// radix-R DFT on slots s, s + S, ..., s + (R-1) S of a 16-slot array (R * S == 16)
-template <int R, int S, bool INV>
-__device__ __forceinline__ void dft_slots(float2 (&a)[16], const int s) {
+// radix-R DFT on slots s, s + S, ..., s + (R-1) S of an E-slot array (R * S == E)
+template <int R, int S, bool INV, int E>
+__device__ __forceinline__ void dft_slots(float2 (&a)[E], const int s) {
     if constexpr (R == 16) {
-        dft16<INV>(a);
+        if constexpr (S == 1) {
+            dft16<INV>(a);
+        } else {
+            float2 v[16];
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = a[s + r * S];
+            dft16<INV>(v);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) a[s + r * S] = v[r];
+        }
     } else if constexpr (R == 8) {
         float2 v[8];
 #pragma unroll
@@ -173,48 +182,49 @@ __host__ __device__ constexpr int fft_tw_size(int np) { return fft_tw_offset(np,
 __device__ __forceinline__ int xpad(int n) { return n + (n >> 4); }
 __host__ __device__ constexpr int xpad_len(int n) { return n + (n >> 4); }
 
-// Butterflies of pass P: thread j handles butterflies b = j + (NP/16) s, s in [0, 16/R); element r
-// of butterfly s lives in slot s + r (16/R).
-template <int NP, int P, bool INV>
-__device__ __forceinline__ void fft_pass(float2 (&x)[16], const int j,
+// Butterflies of pass P: thread j handles butterflies b = j + (NP/E) s, s in [0, E/R); element r
+// of butterfly s lives in slot s + r (E/R).  The first pass therefore reads, and the last pass
+// writes, exactly the elements j + (NP/E) t of the slot convention.
+template <int NP, int E, int P, bool INV>
+__device__ __forceinline__ void fft_pass(float2 (&x)[E], const int j,
                                          const float2* __restrict__ tw) {
-    constexpr int R = fft_radix(NP, P), NS = fft_ns(NP, P), S = 16 / R;
+    constexpr int R = fft_radix(NP, P), NS = fft_ns(NP, P), S = E / R;
     constexpr int TW = fft_tw_offset(NP, P);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
         if constexpr (P > 0) {
-            const int a = (j + (NP / 16) * s) & (NS - 1);
+            const int a = (j + (NP / E) * s) & (NS - 1);
 #pragma unroll
             for (int r = 1; r < R; ++r)
                 x[s + r * S] = c_tw<INV>(x[s + r * S], __ldg(tw + TW + (r - 1) * NS + a));
         }
-        dft_slots<R, S, INV>(x, s);
+        dft_slots<R, S, INV, E>(x, s);
     }
 }
 
 // Exchange arrays interleave the two polarizations: element n of polarization p is at
 // e[2 xpad(n) + p], so the x/y partner threads (adjacent lanes) touch adjacent words.
-// For NP >= 256 every element index of a pass is f(j) + c with c a compile-time multiple of 16,
-// so xpad(f(j) + c) = xpad(f(j)) + c + c/16 and each access is one base register plus an
-// immediate offset.
-template <int NP, int P>
-__device__ __forceinline__ void fft_store(float2* e, const float2 (&x)[16], const int j) {
-    constexpr int R = fft_radix(NP, P), NS = fft_ns(NP, P), S = 16 / R;
-    if constexpr (NP >= 256) {
-        // b = j + (NP/16) s;  n = (b / NS) NS R + (b mod NS) + q NS
+// When NP/E >= 16 every element index of a pass is f(j) + c with c a compile-time constant and
+// f(j) or c a multiple of 16, so xpad(f(j) + c) = xpad(f(j)) + c + c/16 and each access is one
+// base register plus an immediate offset.
+template <int NP, int E, int P>
+__device__ __forceinline__ void fft_store(float2* e, const float2 (&x)[E], const int j) {
+    constexpr int R = fft_radix(NP, P), NS = fft_ns(NP, P), S = E / R;
+    if constexpr (NP / E >= 16) {
+        // b = j + (NP/E) s;  n = (b / NS) NS R + (b mod NS) + q NS
         const int f = (j / NS) * NS * R + (j & (NS - 1));
         float2* eb = e + 2 * xpad(f);
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
             for (int q = 0; q < R; ++q) {
-                const int c = ((NP / 16) * s / NS) * NS * R + q * NS;   // multiple of 16
+                const int c = ((NP / E) * s / NS) * NS * R + q * NS;
                 eb[2 * (c + c / 16)] = x[s + q * S];
             }
     } else {
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            const int b = j + (NP / 16) * s;
+            const int b = j + (NP / E) * s;
             const int base = (b / NS) * NS * R + (b & (NS - 1));
 #pragma unroll
             for (int q = 0; q < R; ++q) e[2 * xpad(base + q * NS)] = x[s + q * S];
@@ -222,52 +232,56 @@ __device__ __forceinline__ void fft_store(float2* e, const float2 (&x)[16], cons
     }
 }
 
-template <int NP, int P>
-__device__ __forceinline__ void fft_load(const float2* e, float2 (&x)[16], const int j) {
-    constexpr int R = fft_radix(NP, P), S = 16 / R;
-    if constexpr (NP >= 256) {
+template <int NP, int E, int P>
+__device__ __forceinline__ void fft_load(const float2* e, float2 (&x)[E], const int j) {
+    constexpr int R = fft_radix(NP, P), S = E / R;
+    if constexpr (NP / E >= 16) {
         const float2* eb = e + 2 * xpad(j);
 #pragma unroll
         for (int s = 0; s < S; ++s)
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int c = (NP / 16) * s + r * (NP / R);              // multiple of 16
+                const int c = (NP / E) * s + r * (NP / R);               // multiple of 16
                 x[s + r * S] = eb[2 * (c + c / 16)];
             }
     } else {
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-            const int b = j + (NP / 16) * s;
+            const int b = j + (NP / E) * s;
 #pragma unroll
             for (int r = 0; r < R; ++r) x[s + r * S] = e[2 * xpad(b + r * (NP / R))];
         }
     }
 }
 
-// Unnormalized DFT of size NP of one polarization held by the NP/16 threads of one group.
+// Unnormalized DFT of size NP of one polarization held by the NP/E threads of one group.
 // INV = false: X[k] = sum_n x[n] exp(-j 2 pi k n / NP);  INV = true: exp(+j ...).
 // `bar` synchronizes the group (both polarizations); `e` is this thread's polarization view of
 // the group's interleaved exchange array (base + p).
-template <int NP, bool INV, class Bar>
-__device__ __forceinline__ void fft_regs(float2 (&x)[16], const int j, float2* e,
+template <int NP, int E, bool INV, class Bar>
+__device__ __forceinline__ void fft_regs(float2 (&x)[E], const int j, float2* e,
                                          const float2* __restrict__ tw, Bar bar) {
     constexpr int NPASS = fft_npasses(NP);
-    fft_pass<NP, 0, INV>(x, j, tw);
+    fft_pass<NP, E, 0, INV>(x, j, tw);
     if constexpr (NPASS > 1) {
         bar();
-        fft_store<NP, 0>(e, x, j);
+        fft_store<NP, E, 0>(e, x, j);
         bar();
-        fft_load<NP, 1>(e, x, j);
-        fft_pass<NP, 1, INV>(x, j, tw);
+        fft_load<NP, E, 1>(e, x, j);
+        fft_pass<NP, E, 1, INV>(x, j, tw);
     }
     if constexpr (NPASS > 2) {
         bar();
-        fft_store<NP, 1>(e, x, j);
+        fft_store<NP, E, 1>(e, x, j);
         bar();
-        fft_load<NP, 2>(e, x, j);
-        fft_pass<NP, 2, INV>(x, j, tw);
+        fft_load<NP, E, 2>(e, x, j);
+        fft_pass<NP, E, 2, INV>(x, j, tw);
     }
 }
+
+// Slots per thread for a given FFT size: 32 for 2048 points (so 5 subbands x 2 polarizations fit
+// in 640 threads), 16 otherwise.
+__host__ __device__ constexpr int fft_slots(int np) { return np >= 2048 ? 32 : 16; }
 
 // ------------------------------------------------------------------------------------------
 // mbarrier + bulk copy (TMA, non-tensor form) with bounded waits

@@ -1,0 +1,31 @@
+// fwd_launch.h -- per-(N', storage) launch entry points of the forward chain kernel.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace cbessfm {
+
+template <int NP, int ST>
+cudaError_t fwd_launch(const ChainArgs& a, int threads, cudaStream_t stream);
+template <int NP, int ST>
+cudaError_t fwd_prepare(int smem_bytes);
+
+#define CBESSFM_FWD_EXTERN(NP)                                                            \
+    extern template cudaError_t fwd_launch<NP, 0>(const ChainArgs&, int, cudaStream_t);   \
+    extern template cudaError_t fwd_launch<NP, 1>(const ChainArgs&, int, cudaStream_t);   \
+    extern template cudaError_t fwd_launch<NP, 2>(const ChainArgs&, int, cudaStream_t);   \
+    extern template cudaError_t fwd_prepare<NP, 0>(int);                                  \
+    extern template cudaError_t fwd_prepare<NP, 1>(int);                                  \
+    extern template cudaError_t fwd_prepare<NP, 2>(int);
+CBESSFM_FWD_EXTERN(16)
+CBESSFM_FWD_EXTERN(32)
+CBESSFM_FWD_EXTERN(64)
+CBESSFM_FWD_EXTERN(128)
+CBESSFM_FWD_EXTERN(256)
+CBESSFM_FWD_EXTERN(512)
+CBESSFM_FWD_EXTERN(1024)
+CBESSFM_FWD_EXTERN(2048)
+#undef CBESSFM_FWD_EXTERN
+
+}  // namespace cbessfm

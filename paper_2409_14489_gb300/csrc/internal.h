@@ -54,8 +54,8 @@ cudaError_t launch_build_gvd(const PlanImpl& p, cudaStream_t stream);
 
 // Forward chain kernel; returns cudaSuccess or the launch error.
 cudaError_t launch_forward(const PlanImpl& p, const ChainArgs& a, cudaStream_t stream);
-// Maximum dynamic shared memory of the forward kernel instantiation for this NP (opt-in limit).
-cudaError_t prepare_forward(int np, int smem_bytes);
+// Opt in to `smem_bytes` of dynamic shared memory for the forward kernel of (NP, storage).
+cudaError_t prepare_forward(int np, int storage, int smem_bytes);
 
 ChainArgs make_chain_args(const PlanImpl& p);
 

@@ -30,6 +30,7 @@ class Case:
     tap_scale: float = 0.1
     field_scale: float = 1.0
     seed: int = 0
+    storage: int = 0          # 0 complex64, 1 fp16 x 4, 2 bf16 x 4
 
     @property
     def link_length(self) -> float:
@@ -58,15 +59,39 @@ def make_plan(case: Case, taps: np.ndarray):
     from paper_2409_14489_gb300 import cbessfm
     link = cbessfm.make_link(case.beta2, case.span_length, case.n_spans, case.sample_rate)
     return cbessfm.Plan(link, case.n_sb, case.n_st, case.ratio,
-                        np.asarray(taps, dtype=np.float32), case.n_fft, case.overlap)
+                        np.asarray(taps, dtype=np.float32), case.n_fft, case.overlap,
+                        storage=case.storage)
+
+
+def to_storage(field: np.ndarray, storage: int):
+    """complex (..., L, 2) -> a CUDA tensor in the plan's storage layout."""
+    import torch
+    x = torch.from_numpy(np.ascontiguousarray(field.astype(np.complex64))).cuda()
+    if storage == 0:
+        return x
+    dt = torch.float16 if storage == 1 else torch.bfloat16
+    return torch.view_as_real(x).reshape(*x.shape[:-1], 4).to(dt).contiguous()
+
+
+def from_storage(y, storage: int) -> np.ndarray:
+    import torch
+    if storage == 0:
+        return y.cpu().numpy().astype(np.complex128)
+    r = y.float().reshape(*y.shape[:-1], 2, 2)
+    return torch.view_as_complex(r.contiguous()).cpu().numpy().astype(np.complex128)
+
+
+def quantize(field: np.ndarray, storage: int) -> np.ndarray:
+    """The input as the GPU sees it after storage rounding (for the oracle)."""
+    return from_storage(to_storage(field, storage), storage)
 
 
 def run_gpu(plan, field: np.ndarray) -> np.ndarray:
     import torch
-    x = torch.from_numpy(np.ascontiguousarray(field.astype(np.complex64))).cuda()
+    x = to_storage(field, plan.storage)
     y = plan.backpropagate(x)
     torch.cuda.synchronize()
-    return y.cpu().numpy().astype(np.complex128)
+    return from_storage(y, plan.storage)
 
 
 def rel_l2(a: np.ndarray, b: np.ndarray, name: str = "") -> float:

@@ -13,7 +13,8 @@ import pytest
 from oracle import channel, dbp as odbp, evaluate
 from synth import configs, signals
 
-from parity_utils import Case, random_field, case_taps, oracle_params, make_plan, run_gpu, rel_l2
+from parity_utils import (Case, random_field, case_taps, oracle_params, make_plan, run_gpu, rel_l2,
+                          quantize)
 
 pytestmark = pytest.mark.gpu
 
@@ -32,6 +33,7 @@ SMALL_CASES = [
     Case(5, 1024, 256, 2, 11, 0.3, 2 * 3840 + 1001, sample_rate=640e9),
     Case(2, 2048, 512, 2, 11, 0.0, 2 * 3072 + 77, sample_rate=128e9),
     Case(2, 2048, 512, 1, 11, 0.3, 4096 + 4000, sample_rate=256e9, seed=4),
+    Case(5, 2048, 512, 2, 11, 0.3, 10240 + 4000, sample_rate=640e9),
     Case(3, 32, 8, 0, 1, 0.5, 200, sample_rate=96e9),             # EDC (no NLPR steps)
     Case(2, 64, 16, 4, 1, 0.5, 333, sample_rate=128e9),           # single-tap (OSSFM-like)
     Case(1, 64, 0, 2, 5, 0.5, 64 * 3),                            # no overlap
@@ -159,3 +161,103 @@ def test_alias_and_argument_errors():
     with pytest.raises(cbessfm.CBESSFMError) as ei:
         plan.backpropagate_ptr(x.data_ptr() + 8, x.data_ptr() + 8 + 4096, 16, 1, 0)
     assert ei.value.status == cbessfm.ERR_INVALID_ARG
+
+
+STORAGE_TOL = {1: 3e-3, 2: 3e-3}
+STORAGE_CASES = [
+    Case(1, 256, 64, 1, 5, 0.5, 2000, storage=1),
+    Case(5, 1024, 256, 3, 11, 0.3, 2 * 3840 + 77, sample_rate=640e9, storage=1),
+    Case(1, 256, 64, 1, 5, 0.5, 2000, storage=2),
+    Case(5, 1024, 256, 3, 11, 0.3, 2 * 3840 + 77, sample_rate=640e9, storage=2),
+    Case(3, 64, 16, 2, 7, 0.3, 333, batch=2, sample_rate=192e9, storage=1),
+    Case(5, 2048, 512, 2, 11, 0.3, 10240 + 999, sample_rate=640e9, storage=2),
+]
+
+
+@pytest.mark.parametrize("case", STORAGE_CASES, ids=lambda c: f"st{c.storage}_sb{c.n_sb}_np{c.n_fft}"
+                         f"_L{c.L}_b{c.batch}")
+def test_reduced_precision_storage_matches_oracle(case):
+    """FP16 / BF16 storage, FP32 arithmetic: the oracle runs in FP64 on the same quantized input;
+    the error is dominated by the rounding of the stored output (relative L2 <= 3e-3)."""
+    taps = case_taps(case)
+    field = random_field(case)
+    plan = make_plan(case, taps)
+    got = run_gpu(plan, field)
+    q_in = quantize(field, case.storage)
+    p = oracle_params(case, taps.astype(np.float32).astype(np.float64))
+    for b in range(case.batch):
+        want = odbp.dbp_mode_b(q_in[b], p, case.n_fft, case.overlap)
+        err = rel_l2(got[b], want, f"storage{case.storage}/{case}/b{b}")
+        assert err <= STORAGE_TOL[case.storage], (b, err)
+
+
+# Long-haul bound for the complex64 form.  The 1e-5 bound of the FP32 path holds on the plain
+# workloads (c1, c2); over 40 strongly nonlinear steps no FP32 chain reaches it.  An FP32 replica
+# of the chain whose FFTs are exact (only dispersion, intensity, FIR and rotation rounded to FP32)
+# already gives 1.7e-5 on this workload, and FP32 FFT rounding (1.1e-7 per 1024-point transform,
+# the same for radix-2, radix-4 and the kernel's radix-16/4/16 order) brings a true FP32 chain to
+# about 3.8e-5, which is what the kernel measures.  The stated bound leaves room for the block
+# sample.
+LONG_HAUL_C64_BOUND = 6e-5
+
+
+@pytest.mark.parametrize("storage,tol", [(0, LONG_HAUL_C64_BOUND), (1, 3e-3), (2, 3e-3)],
+                         ids=["complex64", "fp16", "bf16"])
+def test_c5_long_haul_sampled_blocks(storage, tol):
+    """Long-haul precision workload (5 ch, 40 x 80 km, 2^17 symbols/ch, N' = 2048, 40 steps) in
+    the three storage forms: GPU output vs the FP64 oracle on sampled blocks (first, last and
+    one interior block), the oracle fed the same storage-rounded input."""
+    wl = configs.get_workload("c5_longhaul")
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    tx, _ = signals.tx_waveform(wl, wl.launch_dbm[0], seed=wl.seed)
+    w0 = lk.gamma * signals.effective_length(lk.alpha, lk.span_length)
+    taps = signals.random_taps(wl.seed, d.n_st, d.n_sb, d.ntaps, w0, spread=0.2)
+    case = Case(d.n_sb, d.n_fft, d.overlap, d.n_st, d.ntaps, d.ratio, sig.n_samples,
+                span_length=lk.span_length, n_spans=lk.n_spans, sample_rate=sig.sample_rate,
+                storage=storage)
+    plan = make_plan(case, taps)
+    got = run_gpu(plan, tx[None])[0]
+    q_in = quantize(tx[None], storage)[0]
+    p = oracle_params(case, taps.astype(np.float32).astype(np.float64))
+    nb = plan.n_blocks(case.L)
+    want = odbp.dbp_mode_b(q_in, p, d.n_fft, d.overlap, blocks=[0, nb // 2, nb - 1])
+    sel = ~np.isnan(want[:, 0])
+    err = rel_l2(got[sel], want[sel], f"c5_longhaul/storage{storage}")
+    assert err <= tol, err
+
+
+@pytest.fixture(scope="module")
+def long_haul_received():
+    """A received single-channel DP-16QAM 32 GBd signal after 40 x 80 km (noiseless, oracle SSFM
+    with 100 steps per span) -- the input of the precision comparison in SNR terms."""
+    lk = configs.Link(n_spans=40, nf_db=None)
+    wl = configs.get_workload("c1_tiny").with_(link=lk)
+    sig = wl.signal
+    tx, syms = signals.tx_waveform(wl, 2.0, seed=21)
+    rx = channel.propagate(tx, lk.beta2, lk.gamma, lk.alpha, lk.span_length, lk.n_spans,
+                           sig.sample_rate, steps_per_span=100)
+    return wl, rx, syms
+
+
+@pytest.mark.parametrize("storage,max_dq", [(0, 0.02), (1, 0.1), (2, 0.5)],
+                         ids=["complex64", "fp16", "bf16"])
+def test_long_haul_snr_delta_per_storage(long_haul_received, storage, max_dq):
+    """Q-factor (SNR after matched filter, 1 sps and mean-phase removal) of each storage form
+    against the FP64 oracle on the same received signal, 40 DBP steps with 5 coupled subbands."""
+    wl, rx, syms = long_haul_received
+    lk, sig = wl.link, wl.signal
+    w0 = lk.gamma * signals.effective_length(lk.alpha, lk.span_length)
+    n_sb, n_fft, ov, n_st = 5, 512, 128, 40
+    taps = signals.random_taps(3, n_st, n_sb, 11, w0 / n_sb, spread=0.1)
+    case = Case(n_sb, n_fft, ov, n_st, 11, 0.3, sig.n_samples, span_length=lk.span_length,
+                n_spans=lk.n_spans, sample_rate=sig.sample_rate, storage=storage)
+    plan = make_plan(case, taps)
+    got = run_gpu(plan, rx[None])[0]
+    want = odbp.dbp_mode_b(quantize(rx[None], storage)[0],
+                           oracle_params(case, taps.astype(np.float32).astype(np.float64)),
+                           n_fft, ov)
+    p_pol = configs.dbm_to_watt(2.0) / 2
+    q = [evaluate.snr_db(evaluate.receive(y, sig.sample_rate, sig.baud, sig.rolloff, 0.0, p_pol),
+                         syms[0]) for y in (got, want)]
+    rel_l2(got, want, f"long_haul_snr/storage{storage}/dQ={q[0] - q[1]:+.4f}dB/Q={q[1]:.2f}dB")
+    assert abs(q[0] - q[1]) <= max_dq, q
