@@ -120,6 +120,41 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
                                      int64_t n_samples, int batch, cbessfm_stream stream);
 
 /*
+ * Batched form: many independent jobs, each with its own plan (subbands, steps, taps, N',
+ * overlap, storage), input, output and length, in one persistent launch per group of jobs that
+ * share N', the subband count and the storage type.  Within a group, CTAs claim work items of
+ * consecutive overlap-and-save blocks from a device counter, longest jobs first.
+ */
+typedef struct {
+    const cbessfm_plan* plan;   /* plan of this job; must outlive the batch                      */
+    const void* in;             /* device [n_samples] samples in the plan's storage type          */
+    void* out;                  /* device [n_samples]; must not overlap in                        */
+    int64_t n_samples;          /* one period of this job's sequence                              */
+} cbessfm_job;
+
+typedef struct cbessfm_batch cbessfm_batch;
+
+/*
+ * cbessfm_batch_create -- validate the jobs, build and upload the work list.  Synchronous.
+ * The batch owns its device descriptors (allocated here).  Job buffers are referenced, not
+ * copied: run() processes whatever they hold at the time.
+ */
+cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_batch** out);
+
+/*
+ * cbessfm_batch_run -- process every job: one counter reset and one persistent kernel per group,
+ * asynchronous on `stream`.  It issues no host synchronization and no allocation, so it can be
+ * captured into a CUDA graph and replayed.
+ */
+cbessfm_status cbessfm_batch_run(const cbessfm_batch* batch, cbessfm_stream stream);
+
+/* Number of launch groups and work items of the batch. */
+cbessfm_status cbessfm_batch_info(const cbessfm_batch* batch, int* n_groups, long long* n_items);
+
+/* Release the batch (synchronizes the device first).  NULL is accepted. */
+cbessfm_status cbessfm_batch_destroy(cbessfm_batch* batch);
+
+/*
  * cbessfm_get_status -- synchronize `stream`, then read and clear the plan's device status word
  * (bit 0: a bounded wait for a shared-memory copy gave up -> CBESSFM_ERR_TIMEOUT).
  */

@@ -1,0 +1,141 @@
+"""Project-written autotuner for the per-job launch parameters of the batched form.
+
+For each job shape (subbands, steps, taps, link, sample rate, storage) it picks:
+
+* the per-subband overlap N'_ov: the dispersion memory of the whole link in samples,
+  |beta2| * 2 pi * R * L_link * R (the overlap must cover the channel memory, Sec. III-A), split
+  over the subbands and rounded up to a multiple of 16;
+* the per-subband FFT size N' in {256, 512, 1024, 2048} (N' > N'_ov, the block fitting one SM):
+  ``mode="measure"`` times one launch of each candidate plan on a synthetic block sequence and
+  keeps the lowest time per valid sample; ``mode="model"`` uses the paper's operation count per
+  2D symbol (Eq. (costRM) plus its RA companion) instead and needs no GPU.
+
+Measured choices are cached in a JSON file (``$CBESSFM_AUTOTUNE_CACHE`` or ``_build/autotune.json``
+next to this file), keyed by the job shape.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+from dataclasses import dataclass
+from typing import Dict, Optional, Tuple
+
+from . import cost
+
+CANDIDATE_NFFT = (256, 512, 1024, 2048)
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@dataclass(frozen=True)
+class JobShape:
+    n_sb: int
+    n_st: int
+    ntaps: int
+    beta2: float
+    link_length: float
+    sample_rate: float
+    storage: int = 0
+
+    def key(self) -> str:
+        return (f"sb{self.n_sb}_st{self.n_st}_t{self.ntaps}_b{self.beta2:.4e}_L{self.link_length:.4e}"
+                f"_R{self.sample_rate:.4e}_s{self.storage}")
+
+
+def memory_samples(shape: JobShape) -> float:
+    """Dispersion memory of the link in full-band samples: |beta2| 2 pi R L R."""
+    return abs(shape.beta2) * 2.0 * math.pi * shape.sample_rate * shape.link_length * shape.sample_rate
+
+
+def overlap_for(shape: JobShape) -> int:
+    per_sb = memory_samples(shape) / shape.n_sb
+    return max(16, int(math.ceil(per_sb / 16.0)) * 16)
+
+
+def candidates(shape: JobShape):
+    ov = overlap_for(shape)
+    out = []
+    for nf in CANDIDATE_NFFT:
+        if nf <= ov or shape.ntaps > nf // 2:
+            continue
+        if nf == 2048 and shape.n_sb > 5:
+            continue
+        if nf == 1024 and shape.n_sb > 10:
+            continue
+        out.append((nf, ov))
+    if not out:                     # memory longer than any block: largest block, capped overlap
+        out.append((2048, min(ov, 1536)))
+    return out
+
+
+def model_cost(shape: JobShape, n_fft: int, overlap: int) -> float:
+    """Paper operation count (RM + RA) per valid sample of one block."""
+    N, N_ov = shape.n_sb * n_fft, shape.n_sb * overlap
+    return cost.cbessfm_flops_per_2d(N, N_ov, 2.0, shape.n_sb, shape.n_st)
+
+
+class Autotuner:
+    def __init__(self, mode: str = "measure", cache_path: Optional[str] = None):
+        assert mode in ("measure", "model")
+        self.mode = mode
+        self.cache_path = cache_path or os.environ.get(
+            "CBESSFM_AUTOTUNE_CACHE", os.path.join(_HERE, "_build", "autotune.json"))
+        self.cache: Dict[str, Tuple[int, int]] = {}
+        if mode == "measure" and os.path.exists(self.cache_path):
+            try:
+                with open(self.cache_path) as f:
+                    self.cache = {k: tuple(v) for k, v in json.load(f).items()}
+            except (OSError, ValueError):
+                self.cache = {}
+
+    def choose(self, shape: JobShape) -> Tuple[int, int]:
+        cands = candidates(shape)
+        if self.mode == "model" or len(cands) == 1:
+            return min(cands, key=lambda c: model_cost(shape, *c))
+        k = shape.key()
+        if k not in self.cache:
+            self.cache[k] = self._measure(shape, cands)
+            self._save()
+        return self.cache[k]
+
+    def _save(self):
+        try:
+            os.makedirs(os.path.dirname(self.cache_path), exist_ok=True)
+            with open(self.cache_path, "w") as f:
+                json.dump(self.cache, f, indent=1, sort_keys=True)
+        except OSError:
+            pass
+
+    def _measure(self, shape: JobShape, cands):
+        import numpy as np
+        import torch
+        from . import cbessfm
+        best, best_t = None, float("inf")
+        link = cbessfm.make_link(shape.beta2, shape.link_length, 1, shape.sample_rate)
+        taps = np.zeros((shape.n_st, shape.n_sb, shape.n_sb, shape.ntaps), np.float32)
+        if shape.n_st:
+            taps[..., shape.ntaps // 2] = 1.0
+        for nf, ov in cands:
+            plan = cbessfm.Plan(link, shape.n_sb, shape.n_st, 0.5, taps, nf, ov,
+                                storage=shape.storage)
+            V = plan.valid
+            L = 8 * 152 * V                           # enough blocks to fill the GPU
+            if shape.storage == 0:
+                x = torch.zeros(L, 2, dtype=torch.complex64, device="cuda")
+            else:
+                dt = torch.float16 if shape.storage == 1 else torch.bfloat16
+                x = torch.zeros(L, 4, dtype=dt, device="cuda")
+            y = torch.empty_like(x)
+            for _ in range(2):
+                plan.backpropagate(x, y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                plan.backpropagate(x, y)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 3 / L                 # ms per valid sample
+            if t < best_t:
+                best, best_t = (nf, ov), t
+            plan.close()
+        return best

@@ -39,6 +39,11 @@ class LinkStruct(ctypes.Structure):
                 ("n_spans", ctypes.c_int), ("sample_rate", ctypes.c_double)]
 
 
+class JobStruct(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("n_samples", ctypes.c_int64)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"{_LIB_PATH} is not built: run __graft_entry__.build() "
@@ -64,6 +69,14 @@ def _load():
     lib.cbessfm_last_error.restype = ctypes.c_char_p
     lib.cbessfm_version.argtypes = []
     lib.cbessfm_version.restype = ctypes.c_char_p
+    lib.cbessfm_batch_create.argtypes = [ctypes.POINTER(JobStruct), c_int, ctypes.POINTER(P)]
+    lib.cbessfm_batch_create.restype = c_int
+    lib.cbessfm_batch_run.argtypes = [P, c_void_p]
+    lib.cbessfm_batch_run.restype = c_int
+    lib.cbessfm_batch_info.argtypes = [P, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_longlong)]
+    lib.cbessfm_batch_info.restype = c_int
+    lib.cbessfm_batch_destroy.argtypes = [P]
+    lib.cbessfm_batch_destroy.restype = c_int
     return lib
 
 
@@ -199,3 +212,52 @@ class Plan:
 
 def version() -> str:
     return _lib.cbessfm_version().decode()
+
+
+class Batch:
+    """Batched form (``cbessfm_batch_*``): independent jobs, each ``(plan, x, y)`` with x, y
+    contiguous CUDA tensors in the plan's storage, processed by one persistent launch per group
+    of jobs sharing N', subband count and storage.  ``run()`` is graph-capturable."""
+
+    def __init__(self, jobs):
+        self._jobs = list(jobs)            # keep plans and tensors alive
+        arr = (JobStruct * len(self._jobs))()
+        for k, (plan, x, y) in enumerate(self._jobs):
+            n = x.shape[-2] if x.dim() >= 2 else x.shape[0]
+            arr[k] = JobStruct(plan.handle.value, x.data_ptr(), y.data_ptr(), int(n))
+        self._h = ctypes.c_void_p()
+        _check(_lib.cbessfm_batch_create(arr, len(self._jobs), ctypes.byref(self._h)))
+
+    def run(self, stream=None):
+        _check(_lib.cbessfm_batch_run(self._h, _stream_handle(stream)))
+
+    def info(self):
+        g, n = ctypes.c_int(), ctypes.c_longlong()
+        _check(_lib.cbessfm_batch_info(self._h, ctypes.byref(g), ctypes.byref(n)))
+        return {"groups": g.value, "work_items": n.value}
+
+    def capture(self, warmup: int = 1):
+        """Capture ``run()`` into a torch CUDA graph (after ``warmup`` eager runs); returns the
+        graph, whose ``replay()`` processes the whole batch."""
+        import torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for _ in range(warmup):
+                self.run(s)
+        torch.cuda.current_stream().wait_stream(s)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            self.run()
+        return graph
+
+    def close(self):
+        if self._h:
+            _lib.cbessfm_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -22,6 +22,8 @@ namespace {
 
 thread_local std::string g_last_error;
 
+}  // namespace
+
 cbessfm_status fail(cbessfm_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
@@ -37,9 +39,11 @@ cbessfm_status cuda_fail(cudaError_t e, const char* what) {
                 cudaGetErrorString(e));
 }
 
-constexpr int kMaxDynSmem = 224 * 1024;     // 227 KB per block minus room for static shared memory
-constexpr int kMaxThreads = 640;
-constexpr int kMaxG = 16;
+void clear_error() { g_last_error.clear(); }
+const char* last_error_text() { return g_last_error.c_str(); }
+
+namespace {
+
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
@@ -73,6 +77,21 @@ std::vector<float> pack_taps(const PlanImpl& p, const float* coeffs) {
 
 }  // namespace
 
+int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands) {
+    // about 256 threads, whole warps (G * tb multiple of 32), shared memory and named-barrier
+    // ids (1 + g * bands + i <= 15 when groups span more than one warp)
+    int granule = 1;
+    while ((granule * tb) % 32 != 0) granule *= 2;
+    int G = std::max(granule, (256 / tb) / granule * granule);
+    G = std::min(G, kMaxG);
+    auto fits = [&](int g) {
+        return g * region_bytes <= kMaxDynSmem && g * tb <= kMaxThreads &&
+               !(2 * tpf > 32 && g * bands > 15);
+    };
+    while (G > granule && !fits(G)) G -= granule;
+    return fits(G) ? G : 0;
+}
+
 ChainArgs make_chain_args(const PlanImpl& p) {
     ChainArgs a{};
     a.n_sb = p.n_sb;
@@ -99,20 +118,22 @@ ChainArgs make_chain_args(const PlanImpl& p) {
     return a;
 }
 
+const PlanImpl* plan_impl(const cbessfm_plan* plan) { return plan ? &plan->impl : nullptr; }
+
 }  // namespace cbessfm
 
 using namespace cbessfm;
 
 extern "C" {
 
-const char* cbessfm_last_error(void) { return g_last_error.c_str(); }
+const char* cbessfm_last_error(void) { return cbessfm::last_error_text(); }
 
 const char* cbessfm_version(void) { return "cbessfm-gb300 0.1 (sm_103a)"; }
 
 cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int steps, double ratio,
                                    const float* coeffs, int ntaps, int n_fft, int overlap,
                                    cbessfm_storage storage, cbessfm_plan** out) {
-    g_last_error.clear();
+    clear_error();
     if (out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (link == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "link is NULL");
@@ -174,16 +195,8 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     if (p.region_bytes > kMaxDynSmem)
         return fail(CBESSFM_ERR_UNSUPPORTED, "block of %d samples needs %d B of shared memory",
                     p.N, p.region_bytes);
-    // G blocks per CTA: about 256 threads, whole warps (G * tb multiple of 32), shared memory and
-    // named-barrier ids (1 + g * bands + i <= 15 when groups span more than one warp).
-    int granule = 1;
-    while ((granule * tb) % 32 != 0) granule *= 2;
-    int G = std::max(granule, (256 / tb) / granule * granule);
-    G = std::min(G, kMaxG);
-    while (G > granule && (G * p.region_bytes > kMaxDynSmem || G * tb > kMaxThreads ||
-                           (2 * tpf > 32 && G * bands > 15)))
-        G -= granule;
-    if (G * p.region_bytes > kMaxDynSmem || G * tb > kMaxThreads || (2 * tpf > 32 && G * bands > 15))
+    const int G = choose_blocks_per_cta(tb, p.region_bytes, tpf, bands);
+    if (G < 1)
         return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape fits bands = %d, n_fft = %d", bands, n_fft);
     p.G = G;
     p.threads = G * tb;
@@ -263,7 +276,7 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
 }
 
 cbessfm_status cbessfm_plan_destroy(cbessfm_plan* plan) {
-    g_last_error.clear();
+    clear_error();
     if (plan == nullptr) return CBESSFM_OK;
     cudaDeviceSynchronize();
     free_plan(plan->impl);
@@ -273,7 +286,7 @@ cbessfm_status cbessfm_plan_destroy(cbessfm_plan* plan) {
 
 cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int on_device,
                                   cbessfm_stream stream) {
-    g_last_error.clear();
+    clear_error();
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     PlanImpl& p = plan->impl;
     if (p.n_st == 0) return CBESSFM_OK;
@@ -296,7 +309,7 @@ cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int o
 }
 
 cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_stream stream) {
-    g_last_error.clear();
+    clear_error();
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     if (!(ratio >= 0.0 && ratio <= 1.0)) return fail(CBESSFM_ERR_INVALID_ARG, "ratio must be in [0, 1]");
     plan->impl.ratio = ratio;
@@ -307,7 +320,7 @@ cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_strea
 
 cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, void* out,
                                      int64_t n_samples, int batch, cbessfm_stream stream) {
-    g_last_error.clear();
+    clear_error();
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
     if (n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples must be >= 1");
@@ -334,7 +347,7 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
 }
 
 cbessfm_status cbessfm_get_status(const cbessfm_plan* plan, cbessfm_stream stream) {
-    g_last_error.clear();
+    clear_error();
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned int h = 0;

@@ -1,0 +1,186 @@
+// batch.cu -- batched form: many independent DBP jobs (own plan, length, taps, step count) in
+// one persistent launch per (N', subband count, storage) group.
+//
+// cbessfm_batch_create groups the jobs, cuts every job into work items of G consecutive
+// overlap-and-save blocks, orders each group's items by decreasing cost (longest processing
+// time first: cost = steps + 2 for the entry/exit transforms) and uploads the per-job
+// descriptors and the item lists once.  cbessfm_batch_run then only resets one counter per group
+// and launches the persistent kernels, so the same batch can be captured in a CUDA graph and
+// replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+struct cbessfm_batch {
+    struct Group {
+        int np = 0, n_sb = 0, storage = 0;
+        int G = 1, threads = 0, region_bytes = 0, grid = 0;
+        int item_off = 0, n_items = 0;
+    };
+    std::vector<Group> groups;
+    cbessfm::ChainArgs* d_jobs = nullptr;
+    int2* d_items = nullptr;
+    unsigned int* d_counters = nullptr;
+    int njobs = 0;
+    long long total_items = 0;
+};
+
+namespace cbessfm {
+namespace {
+
+void free_batch(cbessfm_batch* b) {
+    if (!b) return;
+    cudaFree(b->d_jobs);
+    cudaFree(b->d_items);
+    cudaFree(b->d_counters);
+    delete b;
+}
+
+}  // namespace
+}  // namespace cbessfm
+
+using namespace cbessfm;
+
+extern "C" {
+
+cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_batch** out) {
+    clear_error();
+    if (out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (jobs == nullptr || njobs < 1) return fail(CBESSFM_ERR_INVALID_ARG, "no jobs");
+
+    std::vector<ChainArgs> args(njobs);
+    std::map<std::tuple<int, int, int>, std::vector<int>> by_shape;
+    for (int k = 0; k < njobs; ++k) {
+        const cbessfm_job& jb = jobs[k];
+        const PlanImpl* p = plan_impl(jb.plan);
+        if (p == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "job %d: plan is NULL", k);
+        if (jb.in == nullptr || jb.out == nullptr)
+            return fail(CBESSFM_ERR_INVALID_ARG, "job %d: in/out is NULL", k);
+        if (jb.n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "job %d: n_samples < 1", k);
+        if ((reinterpret_cast<uintptr_t>(jb.in) | reinterpret_cast<uintptr_t>(jb.out)) & 15u)
+            return fail(CBESSFM_ERR_INVALID_ARG, "job %d: in/out must be 16-byte aligned", k);
+        const unsigned long long sb = p->storage == CBESSFM_C64 ? 16ull : 8ull;
+        const unsigned long long bytes = (unsigned long long)jb.n_samples * sb;
+        const uintptr_t i0 = reinterpret_cast<uintptr_t>(jb.in), o0 = reinterpret_cast<uintptr_t>(jb.out);
+        if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "job %d: out overlaps in", k);
+        const long long nb = (jb.n_samples + p->V - 1) / p->V;
+        if (nb > (1ll << 30)) return fail(CBESSFM_ERR_UNSUPPORTED, "job %d: too many blocks", k);
+        ChainArgs a = make_chain_args(*p);
+        a.in = jb.in;
+        a.out = jb.out;
+        a.L = jb.n_samples;
+        a.batch = 1;
+        a.n_blocks = (int)nb;
+        args[k] = a;
+        by_shape[std::make_tuple(p->n_fft, p->n_sb, (int)p->storage)].push_back(k);
+    }
+
+    cbessfm_batch* b = new (std::nothrow) cbessfm_batch;
+    if (b == nullptr) return fail(CBESSFM_ERR_OOM, "host allocation of the batch failed");
+    b->njobs = njobs;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    int n_sm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e, "device query");
+    }
+
+    std::vector<int2> items;
+    for (const auto& kv : by_shape) {
+        cbessfm_batch::Group gr;
+        gr.np = std::get<0>(kv.first);
+        gr.n_sb = std::get<1>(kv.first);
+        gr.storage = std::get<2>(kv.first);
+        const int tpf = gr.np / fft_slots(gr.np);
+        const int tb = 2 * gr.n_sb * tpf;
+        for (int k : kv.second) gr.region_bytes = std::max(gr.region_bytes, args[k].region_bytes);
+        gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb);
+        if (gr.G < 1) {
+            free_batch(b);
+            return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape for n_fft %d, bands %d", gr.np, gr.n_sb);
+        }
+        gr.threads = gr.G * tb;
+        // work items: G consecutive blocks of one job, longest processing time first
+        std::vector<std::pair<int, int2>> its;
+        for (int k : kv.second) {
+            const int cost = args[k].n_st + 2;
+            for (int fb = 0; fb < args[k].n_blocks; fb += gr.G) its.push_back({cost, make_int2(k, fb)});
+        }
+        std::stable_sort(its.begin(), its.end(),
+                         [](const std::pair<int, int2>& x, const std::pair<int, int2>& y) { return x.first > y.first; });
+        gr.item_off = (int)items.size();
+        gr.n_items = (int)its.size();
+        for (auto& it : its) items.push_back(it.second);
+        for (int k : kv.second) {
+            args[k].G = gr.G;                       // informational inside the persistent kernel
+            args[k].region_bytes = gr.region_bytes;
+        }
+        int per_sm = 0;
+        e = forward_persistent_occupancy(gr.np, gr.storage, gr.threads, gr.G * gr.region_bytes, &per_sm);
+        if (e != cudaSuccess || per_sm < 1) {
+            free_batch(b);
+            return e != cudaSuccess ? cuda_fail(e, "occupancy") : fail(CBESSFM_ERR_UNSUPPORTED, "persistent kernel does not fit an SM");
+        }
+        gr.grid = (int)std::min<long long>((long long)per_sm * n_sm, gr.n_items);
+        b->groups.push_back(gr);
+    }
+    b->total_items = (long long)items.size();
+
+    e = cudaMalloc(&b->d_jobs, sizeof(ChainArgs) * args.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_items, sizeof(int2) * std::max<size_t>(1, items.size()));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned int) * b->groups.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_jobs, args.data(), sizeof(ChainArgs) * args.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return cuda_fail(e, "batch descriptors");
+    }
+    *out = b;
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_batch_run(const cbessfm_batch* b, cbessfm_stream stream) {
+    clear_error();
+    if (b == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "batch is NULL");
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const cbessfm_batch::Group& gr = b->groups[gi];
+        cudaError_t e = cudaMemsetAsync(b->d_counters + gi, 0, sizeof(unsigned int), st);
+        if (e == cudaSuccess)
+            e = launch_forward_persistent(gr.np, gr.storage, b->d_jobs, b->d_items + gr.item_off,
+                                          gr.n_items, b->d_counters + gi, gr.n_sb, gr.G,
+                                          gr.region_bytes, gr.threads, gr.grid, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    }
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_batch_info(const cbessfm_batch* b, int* n_groups, long long* n_items) {
+    clear_error();
+    if (b == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "batch is NULL");
+    if (n_groups) *n_groups = (int)b->groups.size();
+    if (n_items) *n_items = b->total_items;
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_batch_destroy(cbessfm_batch* b) {
+    clear_error();
+    if (b == nullptr) return CBESSFM_OK;
+    cudaDeviceSynchronize();
+    free_batch(b);
+    return CBESSFM_OK;
+}
+
+}  // extern "C"

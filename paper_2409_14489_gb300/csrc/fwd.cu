@@ -83,6 +83,55 @@ static cudaError_t launch_st(int np, const ChainArgs& a, int threads, cudaStream
     }
 }
 
+template <int ST>
+static cudaError_t persistent_st(int np, const ChainArgs* jobs, const int2* items, int n_items,
+                                 unsigned int* counter, int n_sb, int G, int region_bytes,
+                                 int threads, int grid, cudaStream_t stream) {
+#define CB_CASE(NP)                                                                              \
+    case NP:                                                                                     \
+        return fwd_persistent_launch<NP, ST>(jobs, items, n_items, counter, n_sb, G, region_bytes, \
+                                             threads, grid, stream);
+    switch (np) {
+        CB_CASE(16) CB_CASE(32) CB_CASE(64) CB_CASE(128) CB_CASE(256) CB_CASE(512) CB_CASE(1024)
+        CB_CASE(2048)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CB_CASE
+}
+
+template <int ST>
+static cudaError_t occupancy_st(int np, int threads, int smem_bytes, int* ctas) {
+#define CB_CASE(NP) \
+    case NP: return fwd_persistent_occupancy<NP, ST>(threads, smem_bytes, ctas);
+    switch (np) {
+        CB_CASE(16) CB_CASE(32) CB_CASE(64) CB_CASE(128) CB_CASE(256) CB_CASE(512) CB_CASE(1024)
+        CB_CASE(2048)
+        default: return cudaErrorInvalidValue;
+    }
+#undef CB_CASE
+}
+
+cudaError_t launch_forward_persistent(int np, int storage, const ChainArgs* jobs, const int2* items,
+                                      int n_items, unsigned int* counter, int n_sb, int G,
+                                      int region_bytes, int threads, int grid, cudaStream_t stream) {
+    switch (storage) {
+        case 0: return persistent_st<0>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, threads, grid, stream);
+        case 1: return persistent_st<1>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, threads, grid, stream);
+        case 2: return persistent_st<2>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, threads, grid, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t forward_persistent_occupancy(int np, int storage, int threads, int smem_bytes,
+                                         int* ctas_per_sm) {
+    switch (storage) {
+        case 0: return occupancy_st<0>(np, threads, smem_bytes, ctas_per_sm);
+        case 1: return occupancy_st<1>(np, threads, smem_bytes, ctas_per_sm);
+        case 2: return occupancy_st<2>(np, threads, smem_bytes, ctas_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t prepare_forward(int np, int storage, int smem_bytes) {
     switch (storage) {
         case 0: return prepare_st<0>(np, smem_bytes);

@@ -23,7 +23,6 @@
 
 namespace cbessfm {
 
-constexpr int kMaxG = 16;
 // exp(j theta) by table look-up (the paper computes the exponential with a LUT): theta =
 // 2 pi k / 256 + d with |d| <= pi / 256; the table entry is built in FP64 by the plan and the
 // residual rotation is 1 - d^2/2 + j d (1 - d^2/6), whose truncation error (< 1e-9) is far below
@@ -143,35 +142,46 @@ __device__ __forceinline__ void nlpr_rotation8(const ChainArgs& a, const float* 
 
 // Thread layout of one OLS block (TB = 2 n_sb NP/E threads): rem = 2 jj + p with p the
 // polarization (x/y partners are adjacent lanes) and jj = gi * NP/E + j.
+// Position of a thread in its CTA: block g of the CTA, polarization p, FFT group gi (subband in
+// the steps, polyphase component at entry/exit) and index j within the group.
+struct ThreadPos {
+    int tid, TB, g, rem, p, gi, j;
+};
+
+template <int NP>
+__device__ __forceinline__ ThreadPos thread_pos(int n_sb) {
+    constexpr int TPF = NP / fft_slots(NP);
+    ThreadPos t;
+    t.tid = threadIdx.x;
+    t.TB = 2 * n_sb * TPF;
+    t.g = t.tid / t.TB;
+    t.rem = t.tid - t.g * t.TB;
+    t.p = t.rem & 1;
+    const int jj = t.rem >> 1;
+    t.gi = jj / TPF;
+    t.j = jj - t.gi * TPF;
+    return t;
+}
+
+// The whole CB-ESSFM chain on one overlap-and-save block (block `blk` of sequence `seq` of the
+// job described by `a`), run by the 2 n_sb NP/E threads of CTA slot tp.g.  All threads of the
+// CTA call it together (it contains block-wide barriers); `real` = false runs a zero block and
+// stores nothing.  `bar_g` is the slot's mbarrier, used with phase `parity`.  Returns false if a
+// bounded wait for the staging copy gave up (the caller must then stop).
 template <int NP, int ST>
-__global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) {
+__device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* smem,
+                                            int region_bytes, uint64_t* bar_g, uint32_t parity,
+                                            const float2* __restrict__ s_rot, const ThreadPos& tp,
+                                            bool real, int seq, int blk) {
     using S = Storage<ST>;
     using Pol = typename S::Pol;
     constexpr int E = fft_slots(NP);                   // register slots per thread
     constexpr int TPF = NP / E;                        // threads per (subband, polarization)
     constexpr int XL = 2 * xpad_len(NP);               // float2 per group exchange array
     constexpr int CSL = NP + NP / 16;                  // float2 per (cos, sin) row
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bars[kMaxG];
-    __shared__ float2 s_rot[kRotTable];
-
-    const int tid = threadIdx.x;
-    for (int k = tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
-    const int TB = 2 * a.n_sb * TPF;
-    const int g = tid / TB;
-    const int rem = tid - g * TB;
-    const int p = rem & 1;
-    const int jj = rem >> 1;
-    const int gi = jj / TPF;           // subband (steps) or polyphase component (entry/exit)
-    const int j = jj - gi * TPF;
-    unsigned char* region = smem + (size_t)g * a.region_bytes;
+    const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
+    unsigned char* region = smem + (size_t)g * region_bytes;
     float2* e = reinterpret_cast<float2*>(region) + gi * XL + p;
-
-    const long long total = (long long)a.batch * a.n_blocks;
-    const long long item = (long long)blockIdx.x * a.G + g;
-    const bool real = item < total;
-    const int seq = real ? (int)(item / a.n_blocks) : 0;
-    const int blk = real ? (int)(item % a.n_blocks) : 0;
     const GroupBar<NP, E> bar{1 + g * a.n_sb + gi};
 
     // ---------------- 1. stage the block (circular wrap) ------------------------------------
@@ -182,33 +192,37 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
     const long long start = ((long long)blk * a.V - a.n_ov / 2) % a.L;
     const long long pos0 = start < 0 ? start + a.L : start;
     if constexpr (ST == 0) {
-        if (tid < a.G) mbar_init(&bars[tid], 1);
-        mbar_fence_init();
-        __syncthreads();
-        if (real && rem == 0) {
-            mbar_arrive_expect_tx(&bars[g], (uint32_t)a.N * 16u);
-            long long pos = pos0;
-            const float4* src = reinterpret_cast<const float4*>(a.in) + (long long)seq * a.L;
-            float4* dst4 = reinterpret_cast<float4*>(region);
-            int dst = 0;
-            while (dst < a.N) {
-                const int len = (int)min((long long)(a.N - dst), a.L - pos);
-                bulk_copy_g2s(dst4 + dst, src + pos, (uint32_t)len * 16u, &bars[g]);
-                dst += len;
-                pos = 0;
+        if (rem == 0) {
+            if (real) {
+                // earlier generic-proxy accesses to this region come before the async copy
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar_g, (uint32_t)a.N * 16u);
+                long long pos = pos0;
+                const float4* src = reinterpret_cast<const float4*>(a.in) + (long long)seq * a.L;
+                float4* dst4 = reinterpret_cast<float4*>(region);
+                int dst = 0;
+                while (dst < a.N) {
+                    const int len = (int)min((long long)(a.N - dst), a.L - pos);
+                    bulk_copy_g2s(dst4 + dst, src + pos, (uint32_t)len * 16u, bar_g);
+                    dst += len;
+                    pos = 0;
+                }
+            } else {
+                mbar_arrive(bar_g);                    // complete the phase without a copy
             }
         }
         bool ok = true;
         if (real) {
-            ok = mbar_wait_bounded(&bars[g], 0, kWaitCycles);
+            ok = mbar_wait_bounded(bar_g, parity, kWaitCycles);
         } else {
             float4* z = reinterpret_cast<float4*>(region);
             for (int n = rem; n < a.N; n += TB) z[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+            ok = mbar_wait_bounded(bar_g, parity, kWaitCycles);
         }
         if (__syncthreads_or(!ok)) {
             if (!ok) atomicOr(a.status, kStatusTimeout);
-            if (real) mbar_wait_bounded(&bars[g], 0, kWaitCycles);   // let in-flight copies land
-            return;
+            if (real) mbar_wait_bounded(bar_g, parity, kWaitCycles);   // let in-flight copies land
+            return false;
         }
     } else {
         uint2* st8 = reinterpret_cast<uint2*>(region);
@@ -344,6 +358,67 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
             }
         }
     }
+    return true;
+}
+
+// One launch over `a.batch` sequences of one plan: CTA b runs blocks b G .. b G + G - 1 of the
+// flattened (sequence, block) list.
+template <int NP, int ST>
+__global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[kMaxG];
+    __shared__ float2 s_rot[kRotTable];
+    const ThreadPos tp = thread_pos<NP>(a.n_sb);
+    for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
+    if (tp.tid < a.G) mbar_init(&bars[tp.tid], 1);
+    mbar_fence_init();
+    __syncthreads();
+    const long long total = (long long)a.batch * a.n_blocks;
+    const long long item = (long long)blockIdx.x * a.G + tp.g;
+    const bool real = item < total;
+    const int seq = real ? (int)(item / a.n_blocks) : 0;
+    const int blk = real ? (int)(item % a.n_blocks) : 0;
+    chain_block<NP, ST>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, tp, real, seq, blk);
+}
+
+// Persistent form for a batch of jobs that share N', the subband count and the storage type:
+// CTAs claim work items (job, first block) from `counter` in the order of `items` (sorted by
+// decreasing cost on the host) until the list is exhausted.  Each item runs G consecutive blocks
+// of one job; per-job parameters come from `jobs`.
+template <int NP, int ST>
+__global__ void __launch_bounds__(640, 1) cbessfm_fwd_persistent_kernel(
+    const ChainArgs* __restrict__ jobs, const int2* __restrict__ items, int n_items,
+    unsigned int* __restrict__ counter, int n_sb, int G, int region_bytes) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[kMaxG];
+    __shared__ float2 s_rot[kRotTable];
+    __shared__ ChainArgs s_job;
+    __shared__ int s_item;
+    const ThreadPos tp = thread_pos<NP>(n_sb);
+    if (tp.tid < G) mbar_init(&bars[tp.tid], 1);
+    mbar_fence_init();
+    int rot_of = -1;                               // job whose rotation table is in s_rot
+    for (uint32_t it = 0;; ++it) {
+        if (tp.tid == 0) s_item = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= n_items) break;
+        const int2 w = items[item];
+        for (int k = tp.tid; k < (int)(sizeof(ChainArgs) / sizeof(int)); k += blockDim.x)
+            reinterpret_cast<int*>(&s_job)[k] = reinterpret_cast<const int*>(jobs + w.x)[k];
+        __syncthreads();
+        if (rot_of != w.x) {                           // uniform across the CTA
+            for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(s_job.rot_tbl + k);
+            rot_of = w.x;
+            __syncthreads();
+        }
+        const int blk = w.y + tp.g;
+        const bool real = blk < s_job.n_blocks;
+        if (!chain_block<NP, ST>(s_job, smem, region_bytes, &bars[tp.g], it & 1u, s_rot, tp, real,
+                                 0, real ? blk : 0))
+            return;
+        __syncthreads();                               // s_item / s_job reuse
+    }
 }
 
 // Launch helpers, instantiated per (NP, storage) in the fwd_inst_*.cu translation units.
@@ -359,8 +434,28 @@ cudaError_t fwd_launch(const ChainArgs& a, int threads, cudaStream_t stream) {
 
 template <int NP, int ST>
 cudaError_t fwd_prepare(int smem_bytes) {
-    return cudaFuncSetAttribute(cbessfm_fwd_kernel<NP, ST>,
+    cudaError_t e = cudaFuncSetAttribute(cbessfm_fwd_kernel<NP, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(cbessfm_fwd_persistent_kernel<NP, ST>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+}
+
+template <int NP, int ST>
+cudaError_t fwd_persistent_launch(const ChainArgs* jobs, const int2* items, int n_items,
+                                  unsigned int* counter, int n_sb, int G, int region_bytes,
+                                  int threads, int grid, cudaStream_t stream) {
+    if (n_items <= 0 || grid <= 0) return cudaSuccess;
+    const size_t smem = (size_t)G * region_bytes;
+    cbessfm_fwd_persistent_kernel<NP, ST><<<grid, threads, smem, stream>>>(
+        jobs, items, n_items, counter, n_sb, G, region_bytes);
+    return cudaGetLastError();
+}
+
+template <int NP, int ST>
+cudaError_t fwd_persistent_occupancy(int threads, int smem_bytes, int* ctas_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        ctas_per_sm, cbessfm_fwd_persistent_kernel<NP, ST>, threads, smem_bytes);
 }
 
 }  // namespace cbessfm

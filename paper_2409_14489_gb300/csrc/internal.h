@@ -59,4 +59,27 @@ cudaError_t prepare_forward(int np, int storage, int smem_bytes);
 
 ChainArgs make_chain_args(const PlanImpl& p);
 
+// Launch-shape limits shared by the plan and batch builders.
+constexpr int kMaxDynSmem = 224 * 1024;     // 227 KB per block minus room for static shared memory
+constexpr int kMaxThreads = 640;
+constexpr int kMaxG = 16;
+// OLS blocks per CTA for a block of `tb` threads and `region_bytes` of shared memory (0 = none fits).
+int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands);
+
+// Error reporting (thread-local message, see cbessfm_last_error).
+cbessfm_status fail(cbessfm_status st, const char* fmt, ...);
+cbessfm_status cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+const char* last_error_text();
+
+// The plan object behind the opaque C handle.
+const PlanImpl* plan_impl(const cbessfm_plan* plan);
+
+// Persistent batched launch of the forward kernel for one (NP, storage) group.
+cudaError_t launch_forward_persistent(int np, int storage, const ChainArgs* jobs, const int2* items,
+                                      int n_items, unsigned int* counter, int n_sb, int G,
+                                      int region_bytes, int threads, int grid, cudaStream_t stream);
+cudaError_t forward_persistent_occupancy(int np, int storage, int threads, int smem_bytes,
+                                         int* ctas_per_sm);
+
 }  // namespace cbessfm
