@@ -155,6 +155,27 @@ cbessfm_status cbessfm_batch_info(const cbessfm_batch* batch, int* n_groups, lon
 cbessfm_status cbessfm_batch_destroy(cbessfm_batch* batch);
 
 /*
+ * cbessfm_batch_run_noalloc -- the batched form for callers that cannot allocate device memory
+ * when they run, e.g. a receiver's real-time DSP thread that must not wait on the allocator, a
+ * process whose device memory is reserved up front and capped, or a plugin host that forbids
+ * allocation inside its callbacks.  The paper has no counterpart: this is a deployment variant
+ * of cbessfm_batch_run, computing the same chain with the same per-block arithmetic.
+ *   jobs, njobs  as for cbessfm_batch_create; 1 <= njobs <= 64, all jobs with the same n_fft and
+ *                bands and complex64 storage (else CBESSFM_ERR_UNSUPPORTED with a message);
+ *                in/out are the caller's device buffers.
+ * The work list and counter live in one static device array of 17,152 bytes that every
+ * GPU loading the library holds until exit; nothing is allocated by the call.  The first call on
+ * a device looks up that array's device address and sets the kernel's shared-memory limit, so
+ * make the first call before any stream capture.  The descriptors are copied from host stack
+ * memory with cudaMemcpyAsync, which waits for the stream's earlier work before returning.  All
+ * calls share the array and it keeps the last call's contents (the call clears the counter
+ * itself): calls that overlap on the GPU, from two streams or two threads, race and must be
+ * ordered by the caller.
+ */
+cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int njobs,
+                                         cbessfm_stream stream);
+
+/*
  * cbessfm_get_status -- synchronize `stream`, then read and clear the plan's device status word
  * (bit 0: a bounded wait for a shared-memory copy gave up -> CBESSFM_ERR_TIMEOUT).
  */
