@@ -120,6 +120,44 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
                                      int64_t n_samples, int batch, cbessfm_stream stream);
 
 /*
+ * Differentiation form.  The paper fits its taps offline with finite-difference gradients
+ * (Sec. III-B); these calls give the exact gradient of a real loss L with respect to every
+ * step's taps, the splitting ratio and the input, so the taps and rho can be trained on the
+ * device.  Gradient convention for complex data: G = dL/dRe + j dL/dIm, stored like the field.
+ * complex64 storage only.
+ *
+ * cbessfm_grad_workspace_size -- bytes of device workspace (caller-allocated, 256-byte aligned)
+ *   holding, per overlap-and-save block, n_steps + 2 checkpoints of the block's field and the
+ *   per-block partial gradients.
+ */
+cbessfm_status cbessfm_grad_workspace_size(const cbessfm_plan* plan, int64_t n_samples, int batch,
+                                           size_t* bytes);
+
+/*
+ * cbessfm_backpropagate_checkpointed -- cbessfm_backpropagate that also stores, in `workspace`,
+ * the spectrum after the first GVD, each step's time samples before its rotation and the
+ * spectrum after the last GVD of every block (the adjoint recomputes the rest of each step).
+ */
+cbessfm_status cbessfm_backpropagate_checkpointed(const cbessfm_plan* plan, const void* in, void* out,
+                                                  int64_t n_samples, int batch, void* workspace,
+                                                  size_t ws_bytes, cbessfm_stream stream);
+
+/*
+ * cbessfm_grad -- adjoint of the checkpointed forward whose workspace is passed (same plan, taps,
+ * ratio, n_samples and batch; the workspace must not have been reused in between).
+ *   grad_out     device [batch][n_samples] G of the output (kept samples; gradient is zero on
+ *                samples the forward did not produce).
+ *   grad_coeffs  device double [steps][bands][bands][ntaps]: dL/dw, summed over blocks in FP64.
+ *   grad_ratio   device double scalar dL/drho, or NULL.
+ *   grad_in      device [batch][n_samples] G of the input (overwritten), or NULL.
+ * Per block the adjoint walks the steps backwards: conjugate GVD, inverse transforms, and the
+ * adjoint of the rotation, the coupled-band FIR (transposed taps) and the intensity.
+ */
+cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, double* grad_coeffs,
+                            double* grad_ratio, void* grad_in, void* workspace, size_t ws_bytes,
+                            int64_t n_samples, int batch, cbessfm_stream stream);
+
+/*
  * Batched form: many independent jobs, each with its own plan (subbands, steps, taps, N',
  * overlap, storage), input, output and length, in one persistent launch per group of jobs that
  * share N', the subband count and the storage type.  Within a group, CTAs claim work items of

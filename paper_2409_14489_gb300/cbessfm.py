@@ -69,6 +69,14 @@ def _load():
     lib.cbessfm_last_error.restype = ctypes.c_char_p
     lib.cbessfm_version.argtypes = []
     lib.cbessfm_version.restype = ctypes.c_char_p
+    lib.cbessfm_grad_workspace_size.argtypes = [P, c_int64, c_int, ctypes.POINTER(ctypes.c_size_t)]
+    lib.cbessfm_grad_workspace_size.restype = c_int
+    lib.cbessfm_backpropagate_checkpointed.argtypes = [P, c_void_p, c_void_p, c_int64, c_int,
+                                                       c_void_p, ctypes.c_size_t, c_void_p]
+    lib.cbessfm_backpropagate_checkpointed.restype = c_int
+    lib.cbessfm_grad.argtypes = [P, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 ctypes.c_size_t, c_int64, c_int, c_void_p]
+    lib.cbessfm_grad.restype = c_int
     lib.cbessfm_batch_create.argtypes = [ctypes.POINTER(JobStruct), c_int, ctypes.POINTER(P)]
     lib.cbessfm_batch_create.restype = c_int
     lib.cbessfm_batch_run.argtypes = [P, c_void_p]
@@ -179,6 +187,51 @@ class Plan:
         """Raw-pointer form of ``cbessfm_backpropagate`` (device addresses)."""
         _check(_lib.cbessfm_backpropagate(self._h, in_ptr, out_ptr, n_samples, batch,
                                           stream_handle))
+
+    # ---- differentiation form -------------------------------------------------------------
+    def workspace_size(self, n_samples: int, batch: int = 1) -> int:
+        n = ctypes.c_size_t()
+        _check(_lib.cbessfm_grad_workspace_size(self._h, int(n_samples), int(batch), ctypes.byref(n)))
+        return n.value
+
+    def new_workspace(self, n_samples: int, batch: int = 1):
+        import torch
+        return torch.empty(self.workspace_size(n_samples, batch), dtype=torch.uint8, device="cuda")
+
+    @staticmethod
+    def _shape(x):
+        return (1, x.shape[0]) if x.dim() == 2 else (x.shape[0], x.shape[1])
+
+    def backpropagate_checkpointed(self, x, workspace, out=None, stream=None):
+        """Forward chain that also stores the adjoint's checkpoints in ``workspace``."""
+        import torch
+        if not (x.is_cuda and x.dtype == torch.complex64 and x.is_contiguous()):
+            raise ValueError("x must be a contiguous complex64 CUDA tensor")
+        batch, L = self._shape(x)
+        if out is None:
+            out = torch.empty_like(x)
+        _check(_lib.cbessfm_backpropagate_checkpointed(
+            self._h, x.data_ptr(), out.data_ptr(), L, batch, workspace.data_ptr(),
+            workspace.numel(), _stream_handle(stream)))
+        return out
+
+    def grad(self, grad_out, workspace, want_input: bool = True, stream=None):
+        """Adjoint of the last checkpointed forward: returns (dL/dtaps [steps, bands, bands,
+        ntaps] float64, dL/dratio float64 scalar, dL/din complex64 or None)."""
+        import torch
+        if not (grad_out.is_cuda and grad_out.dtype == torch.complex64):
+            raise ValueError("grad_out must be a complex64 CUDA tensor")
+        g = grad_out.contiguous()
+        batch, L = self._shape(g)
+        gc = torch.zeros((max(self.steps, 0), self.bands, self.bands, self.ntaps),
+                         dtype=torch.float64, device="cuda")
+        gr = torch.zeros((), dtype=torch.float64, device="cuda")
+        gi = torch.empty_like(g) if want_input else None
+        _check(_lib.cbessfm_grad(self._h, g.data_ptr(), gc.data_ptr() if gc.numel() else None,
+                                 gr.data_ptr(), gi.data_ptr() if gi is not None else None,
+                                 workspace.data_ptr(), workspace.numel(), L, batch,
+                                 _stream_handle(stream)))
+        return gc, gr, gi
 
     def set_coeffs(self, coeffs, stream=None):
         import torch

@@ -1,0 +1,591 @@
+// adj.cu -- reverse-mode gradient (adjoint) of the CB-ESSFM chain (differentiation form).
+//
+// The paper trains its taps offline with finite-difference gradients (Sec. III-B) and names
+// automatic differentiation as the way to per-step taps; this file is the hand-written adjoint
+// of the forward chain kernel.  Gradient convention: G_z = dL/dRe(z) + j dL/dIm(z), so a
+// complex-linear map y = A x back-propagates as G_x = A^H G_y.
+//
+// cbessfm_backpropagate_checkpointed runs the forward chain and keeps, per OLS block, the
+// spectrum after the first GVD, each step's time samples before its rotation, and the spectrum
+// after the last GVD.  cbessfm_grad then walks each block backwards, one CTA slot per block:
+//
+//   G_X = DEMUX(DFT_N(G_out on the kept samples))                 (adjoint of MUX + IDFT)
+//   ratio term of the last GVD:   -kdisp * Im(conj(G_X) X_final) summed over bins
+//   for s = N_st-1 .. 0:
+//     G_Y = conj(T_s) G_X ; G_v = IDFT_unnorm(G_Y)                (adjoint of T_s DFT)
+//     recompute u_s (checkpoint), P = |x|^2 + |y|^2, theta, v = u exp(j theta)
+//     G_theta_i[k] = -Im(sum_pol conj(G_v) v)
+//     dL/dw[s][i][l][m] = sum_k G_theta_i[k] P_l[k - m]          (per-block partial)
+//     G_P_l[n] = sum_i sum_m w[s][i][l][m] G_theta_i[n + m]       (FIR with transposed taps)
+//     G_u = exp(-j theta) G_v + 2 G_P u ;  G_X = DFT_unnorm(G_u)
+//   ratio term of the first GVD:  +kdisp * Im(conj(G_X) X_0)
+//   G_in = IDFT_unnorm_N(MUX(conj(T_first) G_X))                  (adjoint of T_first DEMUX DFT)
+//
+// Per-block partial tap gradients (FP32) are summed over blocks in FP64 by a second kernel; the
+// splitting-ratio terms are accumulated in FP64 throughout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fwd_kernel.cuh"
+#include "internal.h"
+
+namespace cbessfm {
+
+// Sum over subbands l and taps of taps_base[(l) * nchunks + c] (float4 chunks) times the rows,
+// for the 8 outputs k0 .. k0 + 7 (the forward FIR's window scheme; rows are swizzled and carry
+// the circular halo).
+template <int E>
+__device__ __forceinline__ void fir8_acc(const ChainArgs& a, const float4* __restrict__ wbase,
+                                         const float* __restrict__ rows0, int k0, float (&acc)[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+    const int m0 = a.H + a.p_off + k0 + a.nc - 3;
+    for (int l = 0; l < a.n_sb; ++l) {
+        const float* pl = rows0 + l * a.pstride;
+        const float4* wrow = wbase + l * a.nchunks;
+        for (int c = 0; c < a.nchunks; ++c) {
+            const float4 w4 = __ldg(wrow + c);
+            const int m = m0 - 4 * c;
+            float win[12];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const float4 v = *reinterpret_cast<const float4*>(pl + pswz<E>(m + 4 * e));
+                win[4 * e] = v.x; win[4 * e + 1] = v.y; win[4 * e + 2] = v.z; win[4 * e + 3] = v.w;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float t = acc[q];
+                t = fmaf(w4.x, win[q + 3], t);
+                t = fmaf(w4.y, win[q + 2], t);
+                t = fmaf(w4.z, win[q + 1], t);
+                t = fmaf(w4.w, win[q], t);
+                acc[q] = t;
+            }
+        }
+    }
+}
+
+// write value v of row sample n (and its circular halo copies) into swizzled row `row`
+template <int NP, int E>
+__device__ __forceinline__ void row_store(float* row, int mb, int n, int H, float v) {
+    row[pswz<E>(mb + n)] = v;
+    if (n < H) row[pswz<E>(mb + n + NP)] = v;
+    if (n >= NP - H) row[pswz<E>(mb + n - NP)] = v;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) {
+    constexpr int E = fft_slots(NP);
+    constexpr int TPF = NP / E;
+    constexpr int XL = 2 * xpad_len(NP);
+    constexpr int CSL = NP + NP / 16;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ float2 s_rot[kRotTable];
+    const ThreadPos tp = thread_pos<NP>(a.n_sb);
+    for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
+    const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
+    const int N = a.N, n_sb = a.n_sb;
+
+    // ---- shared-memory layout of this block's region ----------------------------------------
+    unsigned char* region = smem + (size_t)g * a.region_bytes;
+    float2* e = reinterpret_cast<float2*>(region) + gi * XL + p;          // exchange [0, 17 N)
+    float* prow0 = reinterpret_cast<float*>(region + a.nlpr_off);         // intensity rows
+    float2* csbase = reinterpret_cast<float2*>(prow0 + n_sb * a.pstride); // (cos, sin) rows
+    float* trow0 = reinterpret_cast<float*>(csbase + n_sb * CSL);         // G_theta rows
+    float* gprow0 = trow0 + n_sb * a.pstride;                              // G_P rows [l][n]
+    float* accw = gprow0 + n_sb * NP;                                      // tap-gradient sums
+    const int n_acc = n_sb * n_sb * a.ntaps_pad;
+    double* acc_rho = reinterpret_cast<double*>(accw + n_acc);          // 16-byte aligned slot
+    const int mb = a.H + a.p_off;
+
+    const long long total = (long long)a.batch * a.n_blocks;
+    const long long item = (long long)blockIdx.x * a.G + g;
+    const bool real = item < total;
+    const int seq = real ? (int)(item / a.n_blocks) : 0;
+    const int blk = real ? (int)(item % a.n_blocks) : 0;
+    const long long gblk = real ? item : 0;
+    const GroupBar<NP, E> bar{1 + g * n_sb + gi};
+    const float2* ck = a.ckpt + (size_t)gblk * (size_t)(a.n_st + 2) * 2 * N + (size_t)gi * NP * 2 + p;
+    auto load_ckpt = [&](int c, float2 (&v)[E]) {
+        const float2* src = ck + (size_t)c * 2 * N;
+#pragma unroll
+        for (int t = 0; t < E; ++t) v[t] = src[2 * (j + TPF * t)];
+    };
+    for (int k = rem; k < n_acc + 4; k += TB) accw[k] = 0.f;
+
+    // ---- 1. stage dL/d(out) of the kept samples (zero elsewhere), DFT_N + DEMUX ----------
+    float2* stage = reinterpret_cast<float2*>(region);                    // [N] (x, y) pairs
+    const int lo = a.n_ov / 2;
+    const long long base = (long long)blk * a.V - lo;
+    for (int n = rem; n < 2 * N; n += TB) {
+        const int smp = n >> 1;
+        const long long gidx = base + smp;
+        const bool keep = real && smp >= lo && smp < lo + a.V && gidx < a.L;
+        stage[n] = keep ? a.gout[2 * ((long long)seq * a.L + gidx) + (n & 1)] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    float2 x[E];
+#pragma unroll
+    for (int t = 0; t < E; ++t) x[t] = stage[2 * (n_sb * (j + TPF * t) + gi) + p];
+    __syncthreads();
+    fft_regs<NP, E, false>(x, j, e, a.fft_tw, bar);
+    bar();
+#pragma unroll
+    for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = x[t];
+    __syncthreads();
+    const int ci = -N / 2 + gi * NP + NP / 2;
+    {
+        const float2* eb = reinterpret_cast<const float2*>(region) + p;
+#pragma unroll
+        for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
+        for (int r = 0; r < n_sb; ++r) {
+            const float2* er = eb + r * XL;
+            const float2* wr = a.mix_tw + (size_t)r * N;
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                const int kap = j + TPF * t;
+                int K = ci + (kap < NP / 2 ? kap : kap - NP);
+                K += (K < 0) ? N : 0;
+                x[t] = c_add(x[t], c_mul(er[2 * xpad(K & (NP - 1))], __ldg(wr + K)));
+            }
+        }
+    }
+    __syncthreads();
+    // x now holds G for the spectrum after the last GVD.
+    const float* kd = a.kdisp + (size_t)gi * NP;
+    // the ratio terms cancel strongly across bins: accumulate them in FP64
+    double rho_part = 0.0;
+    if (a.n_st > 0) {
+        // d(T_last)/d(rho) = +j kdisp T_last  ->  Re(conj(G) j kdisp X) = -kdisp Im(conj(G) X)
+        float2 xf[E];
+        load_ckpt(a.n_st + 1, xf);
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const float im = x[t].x * xf[t].y - x[t].y * xf[t].x;      // Im(conj(G) X)
+            rho_part -= (double)__ldg(kd + j + TPF * t) * (double)im;
+        }
+    }
+
+    // ---- 2. steps, last to first ----------------------------------------------------------
+    float2* cs_mine = csbase + gi * CSL;
+    const int k0 = E * j + (E / 2) * p;                                    // FIR outputs k0 ..
+#pragma unroll 1
+    for (int s = a.n_st - 1; s >= 0; --s) {
+        const float2* h = a.gvd + (size_t)((s < a.n_st - 1 ? 1 : 2) * n_sb + gi) * NP;
+#pragma unroll
+        for (int t = 0; t < E; ++t) x[t] = c_mulc(x[t], __ldg(h + j + TPF * t));   // conj(T) G
+        fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);                         // G_v
+        {
+            float2 u[E];
+            load_ckpt(1 + s, u);
+            float* prow = prow0 + gi * a.pstride;
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                float pw = fmaf(u[t].x, u[t].x, u[t].y * u[t].y);
+                pw += __shfl_xor_sync(0xffffffffu, pw, 1);
+                if (p == 0) row_store<NP, E>(prow, mb, j + TPF * t, a.H, pw);
+            }
+        }
+        __syncthreads();
+        {
+            const float4* wb = reinterpret_cast<const float4*>(
+                a.taps + (size_t)(s * n_sb + gi) * n_sb * a.ntaps_pad);
+#pragma unroll
+            for (int h8 = 0; h8 < E / 16; ++h8) {
+                float acc[8];
+                fir8_acc<E>(a, wb, prow0, k0 + 8 * h8, acc);
+                float2* dst = cs_mine + cpad(k0 + 8 * h8);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[q] = rotation_factor(acc[q], s_rot);
+            }
+        }
+        __syncthreads();
+        {
+            // G_theta and the first part of G_u
+            float2 u[E];
+            load_ckpt(1 + s, u);
+            float* trow = trow0 + gi * a.pstride;
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                const float2 cs = cs_mine[cpad(j + TPF * t)];
+                const float2 v = c_mul(u[t], cs);
+                float gt = -(x[t].x * v.y - x[t].y * v.x);                 // -Im(conj(G_v) v)
+                gt += __shfl_xor_sync(0xffffffffu, gt, 1);
+                if (p == 0) row_store<NP, E>(trow, mb, j + TPF * t, a.H, gt);
+                x[t] = c_mulc(x[t], cs);                                    // exp(-j theta) G_v
+            }
+        }
+        __syncthreads();
+        {
+            // dL/dw[s][i][l][m] = sum_k G_theta_i[k] P_l[k - m]: segments of 16 samples of one
+            // (i, l) pair, four taps at a time, summed into the block's accumulators.
+            const int nseg = NP / 16;
+            const int n_work = n_sb * n_sb * nseg;
+            for (int w = rem; w < n_work; w += TB) {
+                const int pair = w / nseg, seg = w - pair * nseg;
+                const int i = pair / n_sb, l = pair - i * n_sb;
+                const int ks = 16 * seg;
+                const float* tr = trow0 + i * a.pstride;
+                const float* pr = prow0 + l * a.pstride;
+                float gth[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) gth[q] = tr[pswz<E>(mb + ks + q)];
+                for (int c = 0; c < a.nchunks; ++c) {
+                    // P_l[k - m] for m = -nc + 4c + d, k = ks + q: window starting at
+                    // ks + nc - 4c - 3 (aligned, as in the forward FIR)
+                    const int m = mb + ks + a.nc - 4 * c - 3;
+                    float win[20];
+#pragma unroll
+                    for (int e4 = 0; e4 < 5; ++e4) {
+                        const float4 v = *reinterpret_cast<const float4*>(pr + pswz<E>(m + 4 * e4));
+                        win[4 * e4] = v.x; win[4 * e4 + 1] = v.y; win[4 * e4 + 2] = v.z; win[4 * e4 + 3] = v.w;
+                    }
+                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        s0 = fmaf(gth[q], win[q + 3], s0);
+                        s1 = fmaf(gth[q], win[q + 2], s1);
+                        s2 = fmaf(gth[q], win[q + 1], s2);
+                        s3 = fmaf(gth[q], win[q], s3);
+                    }
+                    float* acc = accw + (i * n_sb + l) * a.ntaps_pad + 4 * c;
+                    atomicAdd(acc, s0);
+                    atomicAdd(acc + 1, s1);
+                    atomicAdd(acc + 2, s2);
+                    atomicAdd(acc + 3, s3);
+                }
+            }
+            // G_P_l[n] = sum_i sum_m' wt[s][l][i][m'] G_theta_i[n - m'] (transposed taps)
+            const float4* wb = reinterpret_cast<const float4*>(
+                a.taps_t + (size_t)(s * n_sb + gi) * n_sb * a.ntaps_pad);
+#pragma unroll
+            for (int h8 = 0; h8 < E / 16; ++h8) {
+                float acc[8];
+                fir8_acc<E>(a, wb, trow0, k0 + 8 * h8, acc);
+                float4* dst = reinterpret_cast<float4*>(gprow0 + gi * NP + k0 + 8 * h8);
+                dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
+            }
+        }
+        __syncthreads();
+        {
+            // publish and clear this step's tap-gradient sums
+            if (real) {
+                float* gp = a.gpart + (size_t)gblk * ((size_t)a.n_st * n_acc + 4) + (size_t)s * n_acc;
+                for (int k = rem; k < n_acc; k += TB) gp[k] = accw[k];
+            }
+            float2 u[E];
+            load_ckpt(1 + s, u);
+            const float* gpr = gprow0 + gi * NP;
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                const float gp2 = 2.f * gpr[j + TPF * t];
+                x[t] = make_float2(fmaf(gp2, u[t].x, x[t].x), fmaf(gp2, u[t].y, x[t].y));
+            }
+        }
+        __syncthreads();
+        for (int k = rem; k < n_acc; k += TB) accw[k] = 0.f;
+        fft_regs<NP, E, false>(x, j, e, a.fft_tw, bar);                        // G for X_s
+    }
+
+    // ---- 3. first GVD, ratio term, adjoint of entry (MUX + IDFT_N), scatter to G_in ------
+    if (a.n_st > 0) {
+        // d(T_first)/d(rho) = -j kdisp T_first  ->  +kdisp Im(conj(G) X_0)
+        float2 x0[E];
+        load_ckpt(0, x0);
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const float im = x[t].x * x0[t].y - x[t].y * x0[t].x;
+            rho_part += (double)__ldg(kd + j + TPF * t) * (double)im;
+        }
+    }
+    atomicAdd(acc_rho, rho_part);                 // warps may span several small blocks
+    {
+        const float2* h = a.gvd + (size_t)gi * NP;
+#pragma unroll
+        for (int t = 0; t < E; ++t) x[t] = c_mulc(x[t], __ldg(h + j + TPF * t));
+    }
+    __syncthreads();
+    if (real && rem == 0) {
+        float* gp = a.gpart + (size_t)gblk * ((size_t)a.n_st * n_acc + 4) + (size_t)a.n_st * n_acc;
+        *reinterpret_cast<double*>(gp) = *acc_rho;                       // 16-byte aligned
+    }
+    if (a.gin == nullptr) return;                                         // uniform
+    {
+        float2* ex = reinterpret_cast<float2*>(region) + p;
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int kap = j + TPF * t;
+            int K = ci + (kap < NP / 2 ? kap : kap - NP);
+            if (K < 0) K += N;
+            ex[2 * xpad(K)] = x[t];
+        }
+        __syncthreads();
+        const float2* wr = a.mix_tw + (size_t)gi * N;
+#pragma unroll
+        for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
+        for (int q = 0; q < n_sb; ++q) {
+#pragma unroll
+            for (int t = 0; t < E; ++t) {
+                const int K = j + TPF * t + NP * q;
+                x[t] = c_add(x[t], c_mulc(ex[2 * xpad(K)], __ldg(wr + K)));
+            }
+        }
+    }
+    __syncthreads();
+    fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);
+    if (real) {
+        long long pos = base % a.L;
+        if (pos < 0) pos += a.L;
+        float* gin = reinterpret_cast<float*>(a.gin) + 4 * (long long)seq * a.L + 2 * p;
+#pragma unroll
+        for (int t = 0; t < E; ++t) {
+            const int n = n_sb * (j + TPF * t) + gi;
+            long long q = pos + n;
+            q -= (q / a.L) * a.L;
+            atomicAdd(gin + 4 * q, x[t].x);
+            atomicAdd(gin + 4 * q + 1, x[t].y);
+        }
+    }
+}
+
+// FP64 sum of the per-block partial gradients: out[k] = sum_b part[b][k].
+__global__ void reduce_blocks_kernel(const float* __restrict__ part, long long n_blocks, int stride,
+                                     int n_coeffs, double* __restrict__ out_coeffs,
+                                     double* __restrict__ out_ratio) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n_coeffs) return;
+    double acc = 0.0;
+    if (k < n_coeffs) {
+        for (long long b = 0; b < n_blocks; ++b) acc += (double)part[b * stride + k];
+        out_coeffs[k] = acc;
+    } else {
+        // the ratio partial of each block is stored as a double in two float slots
+        for (long long b = 0; b < n_blocks; ++b)
+            acc += *reinterpret_cast<const double*>(part + b * stride + k);
+        if (out_ratio != nullptr) *out_ratio = acc;
+    }
+}
+
+// Per-block tap-gradient sums carry padded tap positions; gather the real ones.
+__global__ void unpad_kernel(const double* __restrict__ padded, int rows, int ntaps_pad, int ntaps,
+                             double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= rows * ntaps) return;
+    const int r = k / ntaps, m = k - r * ntaps;
+    out[k] = padded[(size_t)r * ntaps_pad + m];
+}
+
+// taps_t[s][l][i][q] = taps[s][i][l][ntaps - 1 - q] (zero beyond ntaps)
+__global__ void transpose_taps_kernel(const float* __restrict__ taps, float* __restrict__ taps_t,
+                                      int n_st, int n_sb, int ntaps, int ntaps_pad) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int total = n_st * n_sb * n_sb * ntaps_pad;
+    if (k >= total) return;
+    const int q = k % ntaps_pad;
+    const int rest = k / ntaps_pad;
+    const int i = rest % n_sb;
+    const int l = (rest / n_sb) % n_sb;
+    const int s = rest / (n_sb * n_sb);
+    taps_t[k] = q < ntaps ? taps[((size_t)(s * n_sb + i) * n_sb + l) * ntaps_pad + (ntaps - 1 - q)]
+                          : 0.f;
+}
+
+cudaError_t launch_transpose_taps(const PlanImpl& p, cudaStream_t st) {
+    const int total = p.n_st * p.n_sb * p.n_sb * p.ntaps_pad;
+    if (total == 0) return cudaSuccess;
+    transpose_taps_kernel<<<(total + 255) / 256, 256, 0, st>>>(p.d_taps, p.d_taps_t, p.n_st, p.n_sb,
+                                                               p.ntaps, p.ntaps_pad);
+    return cudaGetLastError();
+}
+
+namespace {
+
+template <int NP, bool ADJ>
+cudaError_t launch_np_adj(const ChainArgs& a, int threads, cudaStream_t st) {
+    const long long total = (long long)a.batch * a.n_blocks;
+    const long long grid = (total + a.G - 1) / a.G;
+    if (grid <= 0) return cudaSuccess;
+    const size_t smem = (size_t)a.G * a.region_bytes;
+    if constexpr (ADJ) {
+        cudaError_t e = cudaFuncSetAttribute(cbessfm_adj_kernel<NP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cbessfm_adj_kernel<NP><<<(unsigned)grid, threads, smem, st>>>(a);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(cbessfm_fwd_ckpt_kernel<NP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        cbessfm_fwd_ckpt_kernel<NP><<<(unsigned)grid, threads, smem, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <bool ADJ>
+cudaError_t dispatch(int np, const ChainArgs& a, int threads, cudaStream_t st) {
+    switch (np) {
+        case 16: return launch_np_adj<16, ADJ>(a, threads, st);
+        case 32: return launch_np_adj<32, ADJ>(a, threads, st);
+        case 64: return launch_np_adj<64, ADJ>(a, threads, st);
+        case 128: return launch_np_adj<128, ADJ>(a, threads, st);
+        case 256: return launch_np_adj<256, ADJ>(a, threads, st);
+        case 512: return launch_np_adj<512, ADJ>(a, threads, st);
+        case 1024: return launch_np_adj<1024, ADJ>(a, threads, st);
+        case 2048: return launch_np_adj<2048, ADJ>(a, threads, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int round_up_i(long long v, int m) { return (int)((v + m - 1) / m * m); }
+
+// Shared-memory region of one block for the adjoint: exchange, intensity, (cos, sin), G_theta,
+// G_P rows and the accumulators.
+int adj_region_bytes(const PlanImpl& p) {
+    const int NP = p.n_fft, nsb = p.n_sb;
+    const long long bytes = round_up_i(16LL * xpad_len(p.N), 128) + 4LL * nsb * p.pstride +
+                            8LL * nsb * xpad_len(NP) + 4LL * nsb * p.pstride + 4LL * nsb * NP +
+                            4LL * (nsb * nsb * p.ntaps_pad + 4);
+    return round_up_i(bytes, 128);
+}
+
+struct Layout {
+    size_t ckpt_bytes, part_bytes, padded_bytes, total;
+    long long n_blk;
+    int part_stride;
+};
+
+Layout layout(const PlanImpl& p, long long n_samples, int batch) {
+    Layout l{};
+    const long long nb = (n_samples + p.V - 1) / p.V;
+    l.n_blk = nb * batch;
+    l.ckpt_bytes = (size_t)l.n_blk * (size_t)(p.n_st + 2) * 16 * p.N;
+    l.part_stride = p.n_st * p.n_sb * p.n_sb * p.ntaps_pad + 4;
+    l.part_bytes = (size_t)l.n_blk * l.part_stride * sizeof(float);
+    l.padded_bytes = ((size_t)l.part_stride * sizeof(double) + 255) / 256 * 256;
+    l.ckpt_bytes = (l.ckpt_bytes + 255) / 256 * 256;
+    l.part_bytes = (l.part_bytes + 255) / 256 * 256;
+    l.total = l.ckpt_bytes + l.part_bytes + l.padded_bytes;
+    return l;
+}
+
+cbessfm_status check_common(const cbessfm_plan* plan, int64_t n_samples, int batch,
+                            const void* workspace, size_t ws_bytes, const PlanImpl** pp) {
+    const PlanImpl* p = plan_impl(plan);
+    if (p == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    if (p->storage != CBESSFM_C64)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "gradients need complex64 storage");
+    if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
+    if (workspace == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u)
+        return fail(CBESSFM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    const Layout l = layout(*p, n_samples, batch);
+    if (ws_bytes < l.total)
+        return fail(CBESSFM_ERR_INVALID_ARG, "workspace of %zu bytes is smaller than %zu", ws_bytes, l.total);
+    if (l.n_blk > (1ll << 31) - 1) return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks");
+    if (adj_region_bytes(*p) > kMaxDynSmem)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "the adjoint of a %d-sample block does not fit shared memory",
+                    p->N);
+    *pp = p;
+    return CBESSFM_OK;
+}
+
+}  // namespace
+}  // namespace cbessfm
+
+using namespace cbessfm;
+
+extern "C" {
+
+cbessfm_status cbessfm_grad_workspace_size(const cbessfm_plan* plan, int64_t n_samples, int batch,
+                                           size_t* bytes) {
+    clear_error();
+    const PlanImpl* p = plan_impl(plan);
+    if (p == nullptr || bytes == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan/bytes is NULL");
+    if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
+    *bytes = layout(*p, n_samples, batch).total;
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_backpropagate_checkpointed(const cbessfm_plan* plan, const void* in, void* out,
+                                                  int64_t n_samples, int batch, void* workspace,
+                                                  size_t ws_bytes, cbessfm_stream stream) {
+    clear_error();
+    const PlanImpl* p = nullptr;
+    cbessfm_status st = check_common(plan, n_samples, batch, workspace, ws_bytes, &p);
+    if (st != CBESSFM_OK) return st;
+    if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u)
+        return fail(CBESSFM_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
+    const unsigned long long bytes = (unsigned long long)n_samples * batch * 16ull;
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
+    if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
+    ChainArgs a = make_chain_args(*p);
+    a.in = in;
+    a.out = out;
+    a.L = n_samples;
+    a.batch = batch;
+    a.n_blocks = (int)((n_samples + p->V - 1) / p->V);
+    a.ckpt = static_cast<float2*>(workspace);
+    const cudaError_t e = dispatch<false>(p->n_fft, a, p->threads, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward launch");
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, double* grad_coeffs,
+                            double* grad_ratio, void* grad_in, void* workspace, size_t ws_bytes,
+                            int64_t n_samples, int batch, cbessfm_stream stream) {
+    clear_error();
+    const PlanImpl* p = nullptr;
+    cbessfm_status st = check_common(plan, n_samples, batch, workspace, ws_bytes, &p);
+    if (st != CBESSFM_OK) return st;
+    if (grad_out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "grad_out is NULL");
+    if ((reinterpret_cast<uintptr_t>(grad_out) | reinterpret_cast<uintptr_t>(grad_in)) & 15u)
+        return fail(CBESSFM_ERR_INVALID_ARG, "grad_out/grad_in must be 16-byte aligned");
+    if (p->n_st > 0 && grad_coeffs == nullptr)
+        return fail(CBESSFM_ERR_INVALID_ARG, "grad_coeffs is NULL");
+    const cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const Layout l = layout(*p, n_samples, batch);
+    unsigned char* ws = static_cast<unsigned char*>(workspace);
+    ChainArgs a = make_chain_args(*p);
+    a.L = n_samples;
+    a.batch = batch;
+    a.n_blocks = (int)((n_samples + p->V - 1) / p->V);
+    a.ckpt = reinterpret_cast<float2*>(ws);
+    a.gpart = reinterpret_cast<float*>(ws + l.ckpt_bytes);
+    a.gout = static_cast<const float2*>(grad_out);
+    a.gin = static_cast<float2*>(grad_in);
+    a.kdisp = p->d_kdisp;
+    a.taps_t = p->d_taps_t;
+    // the adjoint's own region and CTA shape
+    a.region_bytes = adj_region_bytes(*p);
+    a.nlpr_off = round_up_i(16LL * xpad_len(p->N), 128);
+    const int tpf = p->n_fft / fft_slots(p->n_fft);
+    const int tb = 2 * p->n_sb * tpf;
+    a.G = choose_blocks_per_cta(tb, a.region_bytes, tpf, p->n_sb);
+    if (a.G < 1) return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape for the adjoint");
+    cudaError_t e = cudaSuccess;
+    if (grad_in != nullptr)
+        e = cudaMemsetAsync(grad_in, 0, (size_t)n_samples * batch * 16, cs);
+    if (e == cudaSuccess) e = dispatch<true>(p->n_fft, a, a.G * tb, cs);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
+    const int n_coeffs = p->n_st * p->n_sb * p->n_sb * p->ntaps_pad;
+    double* padded = reinterpret_cast<double*>(ws + l.ckpt_bytes + l.part_bytes);
+    // padded[0 .. n_coeffs) = tap sums, padded[n_coeffs] = ratio sum
+    reduce_blocks_kernel<<<(n_coeffs + 1 + 255) / 256, 256, 0, cs>>>(
+        a.gpart, l.n_blk, l.part_stride, n_coeffs, padded, padded + n_coeffs);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && grad_ratio != nullptr)
+        e = cudaMemcpyAsync(grad_ratio, padded + n_coeffs, sizeof(double), cudaMemcpyDeviceToDevice, cs);
+    const int rows = p->n_st * p->n_sb * p->n_sb;
+    if (e == cudaSuccess && rows > 0) {
+        unpad_kernel<<<(rows * p->ntaps + 255) / 256, 256, 0, cs>>>(padded, rows, p->ntaps_pad,
+                                                                  p->ntaps, grad_coeffs);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gradient reduction");
+    return CBESSFM_OK;
+}
+
+}  // extern "C"

@@ -56,6 +56,7 @@ void free_plan(PlanImpl& p) {
     cudaFree(p.d_fft_tw);
     cudaFree(p.d_taps);
     cudaFree(p.d_rot);
+    cudaFree(p.d_taps_t);
     cudaFree(p.d_status);
     p.d_gvd = nullptr;
     p.d_kdisp = nullptr;
@@ -63,6 +64,7 @@ void free_plan(PlanImpl& p) {
     p.d_fft_tw = nullptr;
     p.d_taps = nullptr;
     p.d_rot = nullptr;
+    p.d_taps_t = nullptr;
     p.d_status = nullptr;
 }
 
@@ -245,6 +247,7 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     CB_TRY(cudaMalloc(&p.d_mix_tw, sizeof(float2) * mix_tw.size()), "cudaMalloc(mix)");
     CB_TRY(cudaMalloc(&p.d_fft_tw, sizeof(float2) * fft_tw.size()), "cudaMalloc(fft tw)");
     CB_TRY(cudaMalloc(&p.d_taps, sizeof(float) * n_taps_dev), "cudaMalloc(taps)");
+    CB_TRY(cudaMalloc(&p.d_taps_t, sizeof(float) * n_taps_dev), "cudaMalloc(transposed taps)");
     CB_TRY(cudaMalloc(&p.d_status, sizeof(unsigned int)), "cudaMalloc(status)");
     CB_TRY(cudaMalloc(&p.d_rot, sizeof(float2) * rot.size()), "cudaMalloc(rot)");
     CB_TRY(cudaMemcpy(p.d_rot, rot.data(), sizeof(float2) * rot.size(), cudaMemcpyHostToDevice),
@@ -261,6 +264,7 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
                           cudaMemcpyHostToDevice), "copy taps");
     }
     CB_TRY(launch_build_gvd(p, nullptr), "build GVD tables");
+    CB_TRY(launch_transpose_taps(p, nullptr), "transpose taps");
     CB_TRY(prepare_forward(n_fft, (int)storage, kMaxDynSmem), "set shared-memory limit");
     CB_TRY(cudaDeviceSynchronize(), "plan tables");
 #undef CB_TRY
@@ -304,6 +308,7 @@ cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int o
                               sizeof(float) * p.ntaps, sizeof(float) * p.ntaps,
                               (size_t)p.n_st * p.n_sb * p.n_sb, cudaMemcpyDeviceToDevice, st);
     }
+    if (e == cudaSuccess) e = launch_transpose_taps(p, st);
     if (e != cudaSuccess) return cuda_fail(e, "set_coeffs");
     return CBESSFM_OK;
 }

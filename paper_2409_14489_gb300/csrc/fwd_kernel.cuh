@@ -168,7 +168,7 @@ __device__ __forceinline__ ThreadPos thread_pos(int n_sb) {
 // CTA call it together (it contains block-wide barriers); `real` = false runs a zero block and
 // stores nothing.  `bar_g` is the slot's mbarrier, used with phase `parity`.  Returns false if a
 // bounded wait for the staging copy gave up (the caller must then stop).
-template <int NP, int ST>
+template <int NP, int ST, bool CKPT = false>
 __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* smem,
                                             int region_bytes, uint64_t* bar_g, uint32_t parity,
                                             const float2* __restrict__ s_rot, const ThreadPos& tp,
@@ -183,6 +183,23 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     unsigned char* region = smem + (size_t)g * region_bytes;
     float2* e = reinterpret_cast<float2*>(region) + gi * XL + p;
     const GroupBar<NP, E> bar{1 + g * a.n_sb + gi};
+    // Checkpoints for the adjoint (CKPT): per block, n_st + 2 fields of N complex pairs in the
+    // slot order [c][gi][idx][p]: c = 0 the spectrum after the first GVD, c = 1 + s the time
+    // samples of step s before its rotation, c = n_st + 1 the spectrum after the last GVD.
+    float2* ck = nullptr;
+    if constexpr (CKPT) {
+        ck = a.ckpt + (size_t)((long long)seq * a.n_blocks + blk) * (size_t)(a.n_st + 2) * 2 * a.N +
+             (size_t)gi * NP * 2 + p;
+    }
+    auto save_ckpt = [&](int c, const float2 (&v)[E]) {
+        if constexpr (CKPT) {
+            if (real) {
+                float2* d = ck + (size_t)c * 2 * a.N;
+#pragma unroll
+                for (int t = 0; t < E; ++t) d[2 * (j + TPF * t)] = v[t];
+            }
+        }
+    };
 
     // ---------------- 1. stage the block (circular wrap) ------------------------------------
     // complex64: bulk copies (TMA) completing on an mbarrier, one per contiguous segment.
@@ -274,6 +291,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = c_mul(x[t], __ldg(h + j + TPF * t));
     }
+    save_ckpt(0, x);
     // intensity rows and (cos, sin) rows: after the exchange arrays when they fit (a.sep), else
     // aliased onto them (then two more block-wide barriers per step guard the reuse)
     float* prow0 = reinterpret_cast<float*>(region + a.nlpr_off);
@@ -283,6 +301,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 #pragma unroll 1
     for (int s = 0; s < a.n_st; ++s) {
         fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);            // subband time samples
+        save_ckpt(1 + s, x);
         if (!a.sep) __syncthreads();
         {
             float* prow = prow0 + gi * a.pstride;
@@ -318,6 +337,8 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = c_mul(x[t], __ldg(h + j + TPF * t));
     }
+
+    if (a.n_st > 0) save_ckpt(a.n_st + 1, x);
 
     // ---------------- 4. MUX + inverse full-band DFT + store --------------------------------
     __syncthreads();
@@ -379,6 +400,25 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
     const int seq = real ? (int)(item / a.n_blocks) : 0;
     const int blk = real ? (int)(item % a.n_blocks) : 0;
     chain_block<NP, ST>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, tp, real, seq, blk);
+}
+
+// Forward launch that also writes the adjoint's checkpoints (complex64 storage).
+template <int NP>
+__global__ void __launch_bounds__(640, 1) cbessfm_fwd_ckpt_kernel(const ChainArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bars[kMaxG];
+    __shared__ float2 s_rot[kRotTable];
+    const ThreadPos tp = thread_pos<NP>(a.n_sb);
+    for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
+    if (tp.tid < a.G) mbar_init(&bars[tp.tid], 1);
+    mbar_fence_init();
+    __syncthreads();
+    const long long total = (long long)a.batch * a.n_blocks;
+    const long long item = (long long)blockIdx.x * a.G + tp.g;
+    const bool real = item < total;
+    const int seq = real ? (int)(item / a.n_blocks) : 0;
+    const int blk = real ? (int)(item % a.n_blocks) : 0;
+    chain_block<NP, 0, true>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, tp, real, seq, blk);
 }
 
 // Persistent form for a batch of jobs that share N', the subband count and the storage type:

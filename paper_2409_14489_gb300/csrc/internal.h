@@ -28,6 +28,12 @@ struct ChainArgs {
     const float* taps;           // [n_st][n_sb][n_sb][ntaps_pad]
     const float2* rot_tbl;       // [256] exp(j 2 pi k / 256)
     unsigned int* status;        // device status word
+    float2* ckpt;                // adjoint checkpoints (checkpointed forward only), else null
+    const float* kdisp;          // [n_sb][NP] 2 pi^2 beta2 L_step f^2 (adjoint only)
+    const float* taps_t;         // [n_st][n_sb][n_sb][ntaps_pad] transposed, reversed taps (adjoint)
+    const float2* gout;          // adjoint: dL/d(out) as (re, im) pairs, [batch][L][2]
+    float2* gin;                 // adjoint: dL/d(in), accumulated, or null
+    float* gpart;                // adjoint: per-block partial tap and ratio gradients
 };
 
 struct PlanImpl {
@@ -46,11 +52,15 @@ struct PlanImpl {
     float2* d_fft_tw = nullptr;
     float* d_taps = nullptr;      // [n_st][n_sb][n_sb][ntaps_pad]
     float2* d_rot = nullptr;      // [256] exp(j 2 pi k / 256) from FP64
+    float* d_taps_t = nullptr;    // transposed, reversed taps for the adjoint's intensity gradient
     unsigned int* d_status = nullptr;
 };
 
 // FP64 kernel that fills the three GVD tables (and the ratio-derivative table) on `stream`.
 cudaError_t launch_build_gvd(const PlanImpl& p, cudaStream_t stream);
+
+// taps_t[s][l][i][q] = taps[s][i][l][ntaps - 1 - q]: the adjoint's intensity-gradient filter.
+cudaError_t launch_transpose_taps(const PlanImpl& p, cudaStream_t stream);
 
 // Forward chain kernel; returns cudaSuccess or the launch error.
 cudaError_t launch_forward(const PlanImpl& p, const ChainArgs& a, cudaStream_t stream);
