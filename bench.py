@@ -159,6 +159,94 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------------------
+def _events_ms(fn, steps: int, warmup: int) -> float:
+    """Average CUDA-event time of fn() on the current stream (after warm-up)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def form_batched(steps: int, warmup: int):
+    """Batching form: 256 uneven realizations of the c1 signal model (lengths log-uniform 2^12 ..
+    2^17 symbols, steps in {1,2,4,8,15}, subbands in {1,3,5}, N' and overlap from the measuring
+    autotuner) as one CUDA-graph replay of the persistent per-group launches, next to the same
+    jobs as sequential plain launches."""
+    import dataclasses
+    import torch
+    from paper_2409_14489_gb300 import autotune, cbessfm
+    wl = configs.get_workload("c3_batched")
+    lk, sig, d = wl.link, wl.signal, wl.dbp
+    tuner = autotune.Autotuner("measure")
+    w0 = lk.gamma * signals.effective_length(lk.alpha, lk.span_length)
+    link = cbessfm.make_link(lk.beta2, lk.span_length, lk.n_spans, sig.sample_rate)
+    jobs, sym2d = [], 0
+    for k, jb in enumerate(signals.batch_jobs_c3(wl.seed)):
+        n_fft, ov = tuner.choose(autotune.JobShape(jb["n_sb"], jb["n_st"], d.ntaps, lk.beta2,
+                                                   lk.length, sig.sample_rate))
+        w = wl.with_(signal=dataclasses.replace(sig, n_sym=jb["n_samples"] // 2))
+        tx, _ = signals.tx_waveform(w, 0.0, seed=jb["seed"])
+        taps = signals.random_taps(jb["seed"], jb["n_st"], jb["n_sb"], d.ntaps, w0 / jb["n_st"])
+        plan = cbessfm.Plan(link, jb["n_sb"], jb["n_st"], d.ratio, taps.astype(np.float32),
+                            n_fft, ov)
+        x = torch.from_numpy(tx.astype(np.complex64)).cuda()
+        jobs.append((plan, x, torch.empty_like(x)))
+        sym2d += w.signal.sym2d_per_realization
+    batch = cbessfm.Batch(jobs)
+    graph = batch.capture()
+    t_graph = _events_ms(graph.replay, steps, warmup)
+    t_plain = _events_ms(lambda: [pl.backpropagate(x, y) for pl, x, y in jobs], steps, warmup)
+    info = batch.info()
+    return {"workload": "c3_batched: 256 uneven c1-model realizations, 1x80 km, steps {1,2,4,8,15},"
+                        " subbands {1,3,5}, autotuned N' / overlap",
+            "value": sym2d / (t_graph / 1e3), "unit": UNIT, "ms_per_step": t_graph,
+            "sym2d_per_step": sym2d, "groups": info["groups"], "work_items": info["work_items"],
+            "gpu_launches_per_step": info["groups"],
+            "plain_launches": {"value": sym2d / (t_plain / 1e3), "ms_per_step": t_plain,
+                               "gpu_launches_per_step": len(jobs)},
+            "inputs": "resident, 150 MB total (larger than L2)"}
+
+
+def form_adjoint(steps: int, warmup: int):
+    """Differentiation form: checkpointed forward + adjoint (taps, ratio and input gradients) on
+    32 realizations x 2^15 symbols of the c1 signal model over 15 x 80 km, 5 subbands, 15 steps,
+    11 taps, N' = 1024, N'_ov = 256."""
+    import torch
+    from paper_2409_14489_gb300 import cbessfm
+    wl = configs.get_workload("c4_adjoint")
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    w0 = lk.gamma * signals.effective_length(lk.alpha, lk.span_length)
+    taps = signals.random_taps(wl.seed, d.n_st, d.n_sb, d.ntaps, w0 / d.n_sb)
+    link = cbessfm.make_link(lk.beta2, lk.span_length, lk.n_spans, sig.sample_rate)
+    plan = cbessfm.Plan(link, d.n_sb, d.n_st, d.ratio, taps.astype(np.float32), d.n_fft,
+                        d.overlap)
+    fields = np.stack([signals.tx_waveform(wl, 0.0, seed=100 + b)[0] for b in range(wl.batch)])
+    x = torch.from_numpy(fields.astype(np.complex64)).cuda()
+    y = torch.empty_like(x)
+    gout = torch.randn_like(x) * 0.01
+    ws = plan.new_workspace(sig.n_samples, wl.batch)
+    sym2d = wl.batch * sig.sym2d_per_realization
+
+    def step():
+        plan.backpropagate_checkpointed(x, ws, y)
+        plan.grad(gout, ws, want_input=False)
+
+    t = _events_ms(step, steps, warmup)
+    t_fwd = _events_ms(lambda: plan.backpropagate(x, y), steps, warmup)
+    return {"workload": "c4_adjoint: 32 x 2^15-symbol c1-model realizations, 15x80 km, N_sb=5, "
+                        "N_st=15, 11 taps, N'=1024, N'_ov=256; forward with checkpoints + adjoint",
+            "value": sym2d / (t / 1e3), "unit": UNIT, "ms_per_step": t, "sym2d_per_step": sym2d,
+            "forward_only_ms": t_fwd, "workspace_bytes": int(ws.numel()),
+            "gpu_launches_per_step": 4}
+
+
 def cpu_baseline(wl, taps, fields, budget_s: float = 12.0):
     """The FP64 oracle (mode B) on whole overlap-and-save blocks of realization 0, for about
     ``budget_s`` seconds; returns (2D symbols/s, description)."""
@@ -308,6 +396,15 @@ def run_gpu(args, wl, taps):
         bytes_launch = 2 * fields.nbytes                                   # read + write once
         hbm = float(pk.get("hbm_gbs", FALLBACK["hbm_gbs"]))
         value = world * sym_per_step * args.steps / (total_ms / 1e3)
+        forms = {}
+        try:
+            forms["batched"] = form_batched(max(3, min(args.steps, 10)), 2)
+        except Exception as exc:                       # report, do not lose the main line
+            forms["batched"] = {"error": repr(exc)}
+        try:
+            forms["adjoint"] = form_adjoint(max(3, min(args.steps, 10)), 2)
+        except Exception as exc:
+            forms["adjoint"] = {"error": repr(exc)}
         cpu_val, cpu_desc = cpu_baseline(wl, taps, fields)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -334,6 +431,7 @@ def run_gpu(args, wl, taps):
                     "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
             "gpu_launches": args.steps,
             "clocks": clocks,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
