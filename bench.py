@@ -38,8 +38,9 @@ METRIC = "DBP 2D symbols/s on 1 GB300 (plain vs batched/adjoint) at ≤1e-5 rel.
 UNIT = "2D symbols/s"
 N_SM, FP32_LANES = 152, 128
 FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
-KERNEL_SOURCES = ["paper_2409_14489_gb300/csrc/fwd.cu",
-                  "paper_2409_14489_gb300/csrc/device_common.cuh"]
+KERNEL_SOURCES = ["paper_2409_14489_gb300/csrc/fwd_kernel.cuh",
+                  "paper_2409_14489_gb300/csrc/device_common.cuh",
+                  "paper_2409_14489_gb300/csrc/internal.h"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fwd_kernel_c2_traffic.txt")
 
 

@@ -33,37 +33,14 @@
 
 namespace cbessfm {
 
-// Sum over subbands l and taps of taps_base[(l) * nchunks + c] (float4 chunks) times the rows,
-// for the 8 outputs k0 .. k0 + 7 (the forward FIR's window scheme; rows are swizzled and carry
-// the circular halo).
+// The forward kernel's windowed FIR (fir8) with the 9-to-12-tap fast path.
 template <int E>
 __device__ __forceinline__ void fir8_acc(const ChainArgs& a, const float4* __restrict__ wbase,
                                          const float* __restrict__ rows0, int k0, float (&acc)[8]) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-    const int m0 = a.H + a.p_off + k0 + a.nc - 3;
-    for (int l = 0; l < a.n_sb; ++l) {
-        const float* pl = rows0 + l * a.pstride;
-        const float4* wrow = wbase + l * a.nchunks;
-        for (int c = 0; c < a.nchunks; ++c) {
-            const float4 w4 = __ldg(wrow + c);
-            const int m = m0 - 4 * c;
-            float win[12];
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                const float4 v = *reinterpret_cast<const float4*>(pl + pswz<E>(m + 4 * e));
-                win[4 * e] = v.x; win[4 * e + 1] = v.y; win[4 * e + 2] = v.z; win[4 * e + 3] = v.w;
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float t = acc[q];
-                t = fmaf(w4.x, win[q + 3], t);
-                t = fmaf(w4.y, win[q + 2], t);
-                t = fmaf(w4.z, win[q + 1], t);
-                t = fmaf(w4.w, win[q], t);
-                acc[q] = t;
-            }
-        }
+    if (a.nchunks == 3) {
+        fir8<E, 3>(a, wbase, rows0, k0, acc);
+    } else {
+        fir8<E, 0>(a, wbase, rows0, k0, acc);
     }
 }
 
@@ -95,7 +72,8 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     float2* csbase = reinterpret_cast<float2*>(prow0 + n_sb * a.pstride); // (cos, sin) rows
     float* trow0 = reinterpret_cast<float*>(csbase + n_sb * CSL);         // G_theta rows
     float* gprow0 = trow0 + n_sb * a.pstride;                              // G_P rows [l][n]
-    float* accw = gprow0 + n_sb * NP;                                      // tap-gradient sums
+    float* gtplain = gprow0 + n_sb * NP;                                   // G_theta rows [i][n]
+    float* accw = gtplain + n_sb * NP;                                     // tap-gradient sums
     const int n_acc = n_sb * n_sb * a.ntaps_pad;
     double* acc_rho = reinterpret_cast<double*>(accw + n_acc);          // 16-byte aligned slot
     const int mb = a.H + a.p_off;
@@ -213,48 +191,98 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
                 const float2 v = c_mul(u[t], cs);
                 float gt = -(x[t].x * v.y - x[t].y * v.x);                 // -Im(conj(G_v) v)
                 gt += __shfl_xor_sync(0xffffffffu, gt, 1);
-                if (p == 0) row_store<NP, E>(trow, mb, j + TPF * t, a.H, gt);
+                if (p == 0) {
+                    row_store<NP, E>(trow, mb, j + TPF * t, a.H, gt);
+                    gtplain[gi * NP + j + TPF * t] = gt;
+                }
                 x[t] = c_mulc(x[t], cs);                                    // exp(-j theta) G_v
             }
         }
         __syncthreads();
         {
-            // dL/dw[s][i][l][m] = sum_k G_theta_i[k] P_l[k - m]: segments of 16 samples of one
-            // (i, l) pair, four taps at a time, summed into the block's accumulators.
+            // dL/dw[s][i][l][m] = sum_k G_theta_i[k] P_l[k - m].  Each (i, l) pair is handled by
+            // 16 consecutive lanes; lane `sub` takes the 4-sample chunks k0 = 64 r + 4 sub (its
+            // float4 loads are 16 bytes apart across lanes: no bank conflicts), loads one
+            // intensity window for all 12 taps of the 9-to-12-tap case (4 + 12 - 1 samples), and
+            // accumulates the 12 tap sums in registers; a 16-lane shuffle reduction then gives
+            // each pair's sums to one lane, which stores them.  Other tap counts use the generic
+            // loop below.
             const int nseg = NP / 16;
-            const int n_work = n_sb * n_sb * nseg;
-            for (int w = rem; w < n_work; w += TB) {
-                const int pair = w / nseg, seg = w - pair * nseg;
+            const int n_pairs = n_sb * n_sb;
+            const int lanes = (TB % 16 == 0 && a.nchunks == 3 && NP >= 64) ? TB : 0;
+            for (int base_t = 0; lanes > 0 && base_t < n_pairs * 16; base_t += lanes) {
+                const int t16 = base_t + rem;
+                const bool act = t16 < n_pairs * 16;
+                const int pair = act ? t16 >> 4 : 0, sub = t16 & 15;
                 const int i = pair / n_sb, l = pair - i * n_sb;
-                const int ks = 16 * seg;
-                const float* tr = trow0 + i * a.pstride;
+                const float* gtr = gtplain + i * NP;
                 const float* pr = prow0 + l * a.pstride;
-                float gth[16];
+                float acc[12];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) gth[q] = tr[pswz<E>(mb + ks + q)];
-                for (int c = 0; c < a.nchunks; ++c) {
-                    // P_l[k - m] for m = -nc + 4c + d, k = ks + q: window starting at
-                    // ks + nc - 4c - 3 (aligned, as in the forward FIR)
-                    const int m = mb + ks + a.nc - 4 * c - 3;
-                    float win[20];
+                for (int m = 0; m < 12; ++m) acc[m] = 0.f;
+                if (act) {
+                    for (int k0 = 4 * sub; k0 < NP; k0 += 64) {
+                        const float4 g4 = *reinterpret_cast<const float4*>(gtr + k0);
+                        const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+                        // P_l[k0 + q - m], m = -nc + mi (mi in [0, 12)): window start
+                        // k0 + nc - 11, aligned because (H + p_off + nc + 1) % 4 == 0
+                        const int ws = mb + k0 + a.nc - 11;
+                        float win[16];
 #pragma unroll
-                    for (int e4 = 0; e4 < 5; ++e4) {
-                        const float4 v = *reinterpret_cast<const float4*>(pr + pswz<E>(m + 4 * e4));
-                        win[4 * e4] = v.x; win[4 * e4 + 1] = v.y; win[4 * e4 + 2] = v.z; win[4 * e4 + 3] = v.w;
+                        for (int e4 = 0; e4 < 4; ++e4) {
+                            const float4 v = *reinterpret_cast<const float4*>(pr + pswz<E>(ws + 4 * e4));
+                            win[4 * e4] = v.x; win[4 * e4 + 1] = v.y; win[4 * e4 + 2] = v.z;
+                            win[4 * e4 + 3] = v.w;
+                        }
+#pragma unroll
+                        for (int mi = 0; mi < 12; ++mi)
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[mi] = fmaf(g[q], win[q - mi + 11], acc[mi]);
                     }
-                    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                }
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        s0 = fmaf(gth[q], win[q + 3], s0);
-                        s1 = fmaf(gth[q], win[q + 2], s1);
-                        s2 = fmaf(gth[q], win[q + 1], s2);
-                        s3 = fmaf(gth[q], win[q], s3);
+                for (int mi = 0; mi < 12; ++mi) {
+#pragma unroll
+                    for (int o = 8; o > 0; o >>= 1) acc[mi] += __shfl_xor_sync(0xffffffffu, acc[mi], o);
+                }
+                if (act && sub == 0) {
+                    float* dst = accw + (i * n_sb + l) * a.ntaps_pad;
+#pragma unroll
+                    for (int mi = 0; mi < 12; ++mi) dst[mi] = acc[mi];
+                }
+            }
+            if (lanes == 0) {
+                // blocks narrower than 16 lanes (small N'): one atomic per segment and tap chunk
+                for (int w = rem; w < n_pairs * nseg; w += TB) {
+                    const int pair = w / nseg, seg = w - pair * nseg;
+                    const int i = pair / n_sb, l = pair - i * n_sb;
+                    const int ks = 16 * seg;
+                    const float* tr = trow0 + i * a.pstride;
+                    const float* pr = prow0 + l * a.pstride;
+                    for (int c = 0; c < a.nchunks; ++c) {
+                        const int m = mb + ks + a.nc - 4 * c - 3;
+                        float win[20];
+#pragma unroll
+                        for (int e4 = 0; e4 < 5; ++e4) {
+                            const float4 v = *reinterpret_cast<const float4*>(pr + pswz<E>(m + 4 * e4));
+                            win[4 * e4] = v.x; win[4 * e4 + 1] = v.y; win[4 * e4 + 2] = v.z;
+                            win[4 * e4 + 3] = v.w;
+                        }
+                        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const float gq = tr[pswz<E>(mb + ks + q)];
+                            s0 = fmaf(gq, win[q + 3], s0);
+                            s1 = fmaf(gq, win[q + 2], s1);
+                            s2 = fmaf(gq, win[q + 1], s2);
+                            s3 = fmaf(gq, win[q], s3);
+                        }
+                        float* acc = accw + (i * n_sb + l) * a.ntaps_pad + 4 * c;
+                        atomicAdd(acc, s0);
+                        atomicAdd(acc + 1, s1);
+                        atomicAdd(acc + 2, s2);
+                        atomicAdd(acc + 3, s3);
                     }
-                    float* acc = accw + (i * n_sb + l) * a.ntaps_pad + 4 * c;
-                    atomicAdd(acc, s0);
-                    atomicAdd(acc + 1, s1);
-                    atomicAdd(acc + 2, s2);
-                    atomicAdd(acc + 3, s3);
                 }
             }
             // G_P_l[n] = sum_i sum_m' wt[s][l][i][m'] G_theta_i[n - m'] (transposed taps)
@@ -440,12 +468,12 @@ cudaError_t dispatch(int np, const ChainArgs& a, int threads, cudaStream_t st) {
 
 int round_up_i(long long v, int m) { return (int)((v + m - 1) / m * m); }
 
-// Shared-memory region of one block for the adjoint: exchange, intensity, (cos, sin), G_theta,
-// G_P rows and the accumulators.
+// Shared-memory region of one block for the adjoint: exchange, intensity, (cos, sin), G_theta
+// (swizzled with halo, and plain), G_P rows and the accumulators.
 int adj_region_bytes(const PlanImpl& p) {
     const int NP = p.n_fft, nsb = p.n_sb;
     const long long bytes = round_up_i(16LL * xpad_len(p.N), 128) + 4LL * nsb * p.pstride +
-                            8LL * nsb * xpad_len(NP) + 4LL * nsb * p.pstride + 4LL * nsb * NP +
+                            8LL * nsb * xpad_len(NP) + 4LL * nsb * p.pstride + 8LL * nsb * NP +
                             4LL * (nsb * nsb * p.ntaps_pad + 4);
     return round_up_i(bytes, 128);
 }

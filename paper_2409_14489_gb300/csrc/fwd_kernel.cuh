@@ -101,6 +101,70 @@ __device__ __forceinline__ int cpad(int k) { return k + (k >> 4); }
 // theta_i[k] = sum_l sum_m w[s][i][l][m + nc] P_l[k - m]; stores (cos theta, sin theta).
 // P rows carry a circular halo of H samples on each side, so no index wraps here; each chunk of
 // four taps reads a 12-sample window with aligned 16-byte loads.
+// Windowed FIR of 8 outputs k0 .. k0 + 7 for one output row: acc[q] = sum over rows l and taps
+// of w[l][m] row_l[k0 + q - m] (rows swizzled, with circular halo).  NCH > 0 fixes the number
+// of four-tap chunks at compile time: one window of 8 + 4 NCH samples per row then serves all
+// chunks.  NCH = 0 handles any chunk count with one 12-sample window per chunk.
+template <int E, int NCH>
+__device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restrict__ wbase,
+                                     const float* __restrict__ rows0, int k0, float (&acc)[8]) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+    const int m0 = a.H + a.p_off + k0 + a.nc - 3;      // row index of chunk 0's window
+    for (int l = 0; l < a.n_sb; ++l) {
+        const float* pl = rows0 + l * a.pstride;
+        if constexpr (NCH > 0) {
+            const float4* wrow = wbase + l * NCH;
+            float4 w4[NCH];
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) w4[c] = __ldg(wrow + c);
+            const int m_lo = m0 - 4 * (NCH - 1);
+            float win[8 + 4 * NCH];
+#pragma unroll
+            for (int e = 0; e < 2 + NCH; ++e) {
+                const float4 v = *reinterpret_cast<const float4*>(pl + pswz<E>(m_lo + 4 * e));
+                win[4 * e] = v.x; win[4 * e + 1] = v.y; win[4 * e + 2] = v.z; win[4 * e + 3] = v.w;
+            }
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+                const int off = 4 * (NCH - 1 - c);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float t = acc[q];
+                    t = fmaf(w4[c].x, win[off + q + 3], t);   // m = -nc + 4c
+                    t = fmaf(w4[c].y, win[off + q + 2], t);   // m = -nc + 4c + 1
+                    t = fmaf(w4[c].z, win[off + q + 1], t);
+                    t = fmaf(w4[c].w, win[off + q], t);
+                    acc[q] = t;
+                }
+            }
+        } else {
+            const float4* wrow = wbase + l * a.nchunks;
+            for (int c = 0; c < a.nchunks; ++c) {
+                const float4 w4 = __ldg(wrow + c);
+                const int m = m0 - 4 * c;
+                float win[12];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    const float4 v = *reinterpret_cast<const float4*>(pl + pswz<E>(m + 4 * e));
+                    win[4 * e] = v.x; win[4 * e + 1] = v.y; win[4 * e + 2] = v.z; win[4 * e + 3] = v.w;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float t = acc[q];
+                    t = fmaf(w4.x, win[q + 3], t);
+                    t = fmaf(w4.y, win[q + 2], t);
+                    t = fmaf(w4.z, win[q + 1], t);
+                    t = fmaf(w4.w, win[q], t);
+                    acc[q] = t;
+                }
+            }
+        }
+    }
+}
+
+// Rotation factors for the 8 samples k = k0 .. k0 + 7 of subband i, step s:
+// theta_i[k] = sum_l sum_m w[s][i][l][m + nc] P_l[k - m]; stores (cos theta, sin theta).
 template <int E>
 __device__ __forceinline__ void nlpr_rotation8(const ChainArgs& a, const float* __restrict__ prow0,
                                                float2* __restrict__ cs_row,
@@ -109,39 +173,16 @@ __device__ __forceinline__ void nlpr_rotation8(const ChainArgs& a, const float* 
     const float4* wbase = reinterpret_cast<const float4*>(
         a.taps + (size_t)(s * a.n_sb + i) * a.n_sb * a.ntaps_pad);
     float acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
-    const int m0 = a.H + a.p_off + k0 + a.nc - 3;      // row index of the first window sample
-    for (int l = 0; l < a.n_sb; ++l) {
-        const float* pl = prow0 + l * a.pstride;
-        const float4* wrow = wbase + l * a.nchunks;
-        for (int c = 0; c < a.nchunks; ++c) {
-            const float4 w4 = __ldg(wrow + c);
-            const int m = m0 - 4 * c;
-            float win[12];
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                const float4 v = *reinterpret_cast<const float4*>(pl + pswz<E>(m + 4 * e));
-                win[4 * e] = v.x; win[4 * e + 1] = v.y; win[4 * e + 2] = v.z; win[4 * e + 3] = v.w;
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float t = acc[q];
-                t = fmaf(w4.x, win[q + 3], t);   // m = -nc + 4c
-                t = fmaf(w4.y, win[q + 2], t);   // m = -nc + 4c + 1
-                t = fmaf(w4.z, win[q + 1], t);
-                t = fmaf(w4.w, win[q], t);
-                acc[q] = t;
-            }
-        }
+    if (a.nchunks == 3) {
+        fir8<E, 3>(a, wbase, prow0, k0, acc);           // 9 to 12 taps
+    } else {
+        fir8<E, 0>(a, wbase, prow0, k0, acc);
     }
     float2* dst = cs_row + cpad(k0);                   // k0 % 16 in {0, 8}: no carry below
 #pragma unroll
     for (int q = 0; q < 8; ++q) dst[q] = rotation_factor(acc[q], rot_tbl);
 }
 
-// Thread layout of one OLS block (TB = 2 n_sb NP/E threads): rem = 2 jj + p with p the
-// polarization (x/y partners are adjacent lanes) and jj = gi * NP/E + j.
 // Position of a thread in its CTA: block g of the CTA, polarization p, FFT group gi (subband in
 // the steps, polyphase component at entry/exit) and index j within the group.
 struct ThreadPos {
@@ -306,16 +347,28 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         {
             float* prow = prow0 + gi * a.pstride;
             const int mb = a.H + a.p_off;
+            // With E = 16 the swizzle period is 64 floats: for NP/E a multiple of 64 every slot's
+            // row index is base + (NP/E) t with one XOR constant, so the stores use immediate
+            // offsets; the halo (H <= NP/E) can only meet slots 0 and E - 1.
+            constexpr bool kFlat = (E == 16) && (TPF % 64 == 0);
+            const bool flat = kFlat && a.H <= TPF;
+            float* pbase = prow + pswz<E>(mb + j);
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 float pw = fmaf(x[t].x, x[t].x, x[t].y * x[t].y);
                 pw += __shfl_xor_sync(0xffffffffu, pw, 1);          // |x|^2 + |y|^2
                 if (p == 0) {
                     const int n = j + TPF * t;
-                    prow[pswz<E>(mb + n)] = pw;
-                    // circular halo: H <= NP (ntaps <= NP/2), so one copy per side suffices
-                    if (n < a.H) prow[pswz<E>(mb + n + NP)] = pw;
-                    if (n >= NP - a.H) prow[pswz<E>(mb + n - NP)] = pw;
+                    if (flat) {
+                        pbase[TPF * t] = pw;
+                        if (t == 0 && n < a.H) prow[pswz<E>(mb + n + NP)] = pw;
+                        if (t == E - 1 && n >= NP - a.H) prow[pswz<E>(mb + n - NP)] = pw;
+                    } else {
+                        prow[pswz<E>(mb + n)] = pw;
+                        // circular halo: H <= NP (ntaps <= NP/2), so one copy per side suffices
+                        if (n < a.H) prow[pswz<E>(mb + n + NP)] = pw;
+                        if (n >= NP - a.H) prow[pswz<E>(mb + n - NP)] = pw;
+                    }
                 }
             }
         }
