@@ -443,10 +443,11 @@ cudaError_t launch_np_adj(const ChainArgs& a, int threads, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         cbessfm_adj_kernel<NP><<<(unsigned)grid, threads, smem, st>>>(a);
     } else {
+        const size_t smem_f = smem + a.tbl_bytes;        // + the chain's per-CTA tables
         cudaError_t e = cudaFuncSetAttribute(cbessfm_fwd_ckpt_kernel<NP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_f);
         if (e != cudaSuccess) return e;
-        cbessfm_fwd_ckpt_kernel<NP><<<(unsigned)grid, threads, smem, st>>>(a);
+        cbessfm_fwd_ckpt_kernel<NP><<<(unsigned)grid, threads, smem_f, st>>>(a);
     }
     return cudaGetLastError();
 }

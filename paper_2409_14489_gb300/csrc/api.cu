@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -79,7 +80,7 @@ std::vector<float> pack_taps(const PlanImpl& p, const float* coeffs) {
 
 }  // namespace
 
-int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands) {
+int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands, int extra_bytes) {
     // about 256 threads, whole warps (G * tb multiple of 32), shared memory and named-barrier
     // ids (1 + g * bands + i <= 15 when groups span more than one warp)
     int granule = 1;
@@ -87,11 +88,85 @@ int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands) {
     int G = std::max(granule, (256 / tb) / granule * granule);
     G = std::min(G, kMaxG);
     auto fits = [&](int g) {
-        return g * region_bytes <= kMaxDynSmem && g * tb <= kMaxThreads &&
+        return g * region_bytes + extra_bytes <= kMaxDynSmem && g * tb <= kMaxThreads &&
                !(2 * tpf > 32 && g * bands > 15);
     };
     while (G > granule && !fits(G)) G -= granule;
     return fits(G) ? G : 0;
+}
+
+// OLS blocks resident per SM for G blocks of `tb` threads per CTA and `region` bytes each: the
+// forward kernels are compiled for 640 threads at 96 registers, so registers bound the CTAs too.
+int resident_blocks(int G, int tb, int region, int tables) {
+    if (G < 1) return 0;
+    const int smem_per_cta = G * region + tables + 4096;         // + static shared memory
+    const int by_smem = (228 * 1024) / smem_per_cta;
+    const int by_regs = 65536 / (G * tb * 96);
+    return G * std::min(by_smem, by_regs);
+}
+
+bool choose_layout(PlanImpl& p, int tb, int tpf) {
+    const int bands = p.n_sb, n_fft = p.n_fft;
+    const int exch = round_up(std::max(16 * p.N, 16 * xpad_len(p.N)), 128);  // staging fits too
+    const int prow = round_up(4 * bands * p.pstride, 128);
+    const int csr = round_up(8 * bands * xpad_len(n_fft), 128);
+    struct Cand {
+        int layout, region, nlpr_off, exb_off, pbuf;
+    };
+    std::vector<Cand> cands;
+    // ping-pong exchange arrays with two intensity buffers, then with one
+    cands.push_back({kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, prow});
+    cands.push_back({kLayoutPingPong, 2 * exch + prow, 2 * exch, exch, 0});
+    cands.push_back({kLayoutSeparate, exch + prow + csr, exch, 0, 0});
+    cands.push_back({kLayoutAlias, round_up(std::max(exch, prow + csr), 128), 0, 0, 0});
+    // Optional override of the automatic choice (tuning): CBESSFM_SMEM_LAYOUT = pingpong2 |
+    // pingpong1 | separate | alias.  A layout that does not fit falls back to the automatic one.
+    int forced = -1;
+    if (const char* env = std::getenv("CBESSFM_SMEM_LAYOUT")) {
+        const char* names[4] = {"pingpong2", "pingpong1", "separate", "alias"};
+        for (int k = 0; k < 4; ++k)
+            if (std::strcmp(env, names[k]) == 0) forced = k;
+    }
+    // per-CTA tables: FFT twiddles always, one step's taps (double-buffered) for 9 to 12 taps
+    const int tw = chain_tw_bytes(fft_tw_size(n_fft));
+    const int tw_taps = tw + (p.nchunks == 3 ? chain_taps_bytes(bands) : 0);
+    int best = -1, best_res = 0, best_G = 0, best_tbl = 0;
+    for (int k = 0; k < (int)cands.size(); ++k) {
+        const Cand& c = cands[k];
+        int tbl = tw_taps;
+        int G = choose_blocks_per_cta(tb, c.region, tpf, bands, tbl);
+        if (G < 1 && tbl != tw) {
+            tbl = tw;
+            G = choose_blocks_per_cta(tb, c.region, tpf, bands, tbl);
+        }
+        if (G < 1) continue;
+        const int res = resident_blocks(G, tb, c.region, tbl);
+        if (k == forced) {
+            best = k;
+            best_G = G;
+            best_tbl = tbl;
+            break;
+        }
+        // candidates are in order of preference: a later one wins only with more resident blocks
+        if (best < 0 || res > best_res) {
+            best = k;
+            best_res = res;
+            best_G = G;
+            best_tbl = tbl;
+        }
+    }
+    if (best < 0) return false;
+    const Cand& c = cands[best];
+    p.tbl_bytes = best_tbl;
+    p.taps_smem = best_tbl != tw ? 1 : 0;
+    p.layout = c.layout;
+    p.region_bytes = c.region;
+    p.nlpr_off = c.nlpr_off;
+    p.exb_off = c.exb_off;
+    p.pbuf_bytes = c.pbuf;
+    p.G = best_G;
+    p.threads = best_G * tb;
+    return true;
 }
 
 ChainArgs make_chain_args(const PlanImpl& p) {
@@ -110,7 +185,11 @@ ChainArgs make_chain_args(const PlanImpl& p) {
     a.pstride = p.pstride;
     a.region_bytes = p.region_bytes;
     a.nlpr_off = p.nlpr_off;
-    a.sep = p.sep;
+    a.layout = p.layout;
+    a.exb_off = p.exb_off;
+    a.pbuf_bytes = p.pbuf_bytes;
+    a.tbl_bytes = p.tbl_bytes;
+    a.taps_smem = p.taps_smem;
     a.gvd = p.d_gvd;
     a.mix_tw = p.d_mix_tw;
     a.fft_tw = p.d_fft_tw;
@@ -181,27 +260,9 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     const int tb = 2 * bands * tpf;                 // one polarization per thread
     if (tb > kMaxThreads)
         return fail(CBESSFM_ERR_UNSUPPORTED, "%d threads per block exceed %d", tb, kMaxThreads);
-    const int need_stage = 16 * p.N;
-    const int need_exch = 16 * xpad_len(p.N);
-    const int need_nlpr = 4 * bands * p.pstride + 8 * bands * xpad_len(n_fft);  // P + (cos, sin)
-    const int base = round_up(std::max(need_stage, need_exch), 128);
-    if (base + round_up(need_nlpr, 128) <= kMaxDynSmem) {
-        p.sep = 1;                                    // separate rows: fewer barriers per step
-        p.nlpr_off = base;
-        p.region_bytes = base + round_up(need_nlpr, 128);
-    } else {
-        p.sep = 0;
-        p.nlpr_off = 0;
-        p.region_bytes = round_up(std::max(base, need_nlpr), 128);
-    }
-    if (p.region_bytes > kMaxDynSmem)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "block of %d samples needs %d B of shared memory",
-                    p.N, p.region_bytes);
-    const int G = choose_blocks_per_cta(tb, p.region_bytes, tpf, bands);
-    if (G < 1)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape fits bands = %d, n_fft = %d", bands, n_fft);
-    p.G = G;
-    p.threads = G * tb;
+    if (!choose_layout(p, tb, tpf))
+        return fail(CBESSFM_ERR_UNSUPPORTED, "no shared-memory layout fits bands = %d, n_fft = %d",
+                    bands, n_fft);
 
     cudaError_t e = cudaGetDevice(&p.device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");

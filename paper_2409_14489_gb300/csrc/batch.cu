@@ -21,7 +21,7 @@
 struct cbessfm_batch {
     struct Group {
         int np = 0, n_sb = 0, storage = 0;
-        int G = 1, threads = 0, region_bytes = 0, grid = 0;
+        int G = 1, threads = 0, region_bytes = 0, tbl_bytes = 0, grid = 0;
         int item_off = 0, n_items = 0;
     };
     std::vector<Group> groups;
@@ -103,8 +103,19 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
         gr.storage = std::get<2>(kv.first);
         const int tpf = gr.np / fft_slots(gr.np);
         const int tb = 2 * gr.n_sb * tpf;
-        for (int k : kv.second) gr.region_bytes = std::max(gr.region_bytes, args[k].region_bytes);
-        gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb);
+        bool any_taps = false;
+        for (int k : kv.second) {
+            gr.region_bytes = std::max(gr.region_bytes, args[k].region_bytes);
+            any_taps = any_taps || args[k].taps_smem;
+        }
+        // per-CTA tables: twiddles, plus the tap buffers if a job stages its taps and they fit
+        const int tw = chain_tw_bytes(fft_tw_size(gr.np));
+        gr.tbl_bytes = tw + (any_taps ? chain_taps_bytes(gr.n_sb) : 0);
+        gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb, gr.tbl_bytes);
+        if (gr.G < 1 && any_taps) {
+            gr.tbl_bytes = tw;
+            gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb, gr.tbl_bytes);
+        }
         if (gr.G < 1) {
             free_batch(b);
             return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape for n_fft %d, bands %d", gr.np, gr.n_sb);
@@ -124,9 +135,12 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
         for (int k : kv.second) {
             args[k].G = gr.G;                       // informational inside the persistent kernel
             args[k].region_bytes = gr.region_bytes;
+            args[k].tbl_bytes = gr.tbl_bytes;
+            if (gr.tbl_bytes == tw) args[k].taps_smem = 0;
         }
         int per_sm = 0;
-        e = forward_persistent_occupancy(gr.np, gr.storage, gr.threads, gr.G * gr.region_bytes, &per_sm);
+        e = forward_persistent_occupancy(gr.np, gr.storage, gr.threads,
+                                         gr.G * gr.region_bytes + gr.tbl_bytes, &per_sm);
         if (e != cudaSuccess || per_sm < 1) {
             free_batch(b);
             return e != cudaSuccess ? cuda_fail(e, "occupancy") : fail(CBESSFM_ERR_UNSUPPORTED, "persistent kernel does not fit an SM");
@@ -161,7 +175,7 @@ cbessfm_status cbessfm_batch_run(const cbessfm_batch* b, cbessfm_stream stream) 
         if (e == cudaSuccess)
             e = launch_forward_persistent(gr.np, gr.storage, b->d_jobs, b->d_items + gr.item_off,
                                           gr.n_items, b->d_counters + gi, gr.n_sb, gr.G,
-                                          gr.region_bytes, gr.threads, gr.grid, st);
+                                          gr.region_bytes, gr.tbl_bytes, gr.threads, gr.grid, st);
         if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     }
     return CBESSFM_OK;

@@ -185,7 +185,8 @@ __host__ __device__ constexpr int xpad_len(int n) { return n + (n >> 4); }
 // Butterflies of pass P: thread j handles butterflies b = j + (NP/E) s, s in [0, E/R); element r
 // of butterfly s lives in slot s + r (E/R).  The first pass therefore reads, and the last pass
 // writes, exactly the elements j + (NP/E) t of the slot convention.
-template <int NP, int E, int P, bool INV>
+// TWS: the twiddle table `tw` is in shared memory (plain loads) instead of global memory.
+template <int NP, int E, int P, bool INV, bool TWS = false>
 __device__ __forceinline__ void fft_pass(float2 (&x)[E], const int j,
                                          const float2* __restrict__ tw) {
     constexpr int R = fft_radix(NP, P), NS = fft_ns(NP, P), S = E / R;
@@ -195,8 +196,20 @@ __device__ __forceinline__ void fft_pass(float2 (&x)[E], const int j,
         if constexpr (P > 0) {
             const int a = (j + (NP / E) * s) & (NS - 1);
 #pragma unroll
-            for (int r = 1; r < R; ++r)
-                x[s + r * S] = c_tw<INV>(x[s + r * S], __ldg(tw + TW + (r - 1) * NS + a));
+            for (int r = 1; r < R; ++r) {
+                const float2* w = tw + TW + (r - 1) * NS + a;
+                float2 wv;
+                if constexpr (TWS) {
+                    // volatile: keeps each load at its use (plain loads of the table let the
+                    // compiler keep twiddles live across passes, at the cost of spills)
+                    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                                 : "=f"(wv.x), "=f"(wv.y)
+                                 : "r"(static_cast<uint32_t>(__cvta_generic_to_shared(w))));
+                } else {
+                    wv = __ldg(w);
+                }
+                x[s + r * S] = c_tw<INV>(x[s + r * S], wv);
+            }
         }
         dft_slots<R, S, INV, E>(x, s);
     }
@@ -256,27 +269,36 @@ __device__ __forceinline__ void fft_load(const float2* e, float2 (&x)[E], const 
 
 // Unnormalized DFT of size NP of one polarization held by the NP/E threads of one group.
 // INV = false: X[k] = sum_n x[n] exp(-j 2 pi k n / NP);  INV = true: exp(+j ...).
-// `bar` synchronizes the group (both polarizations); `e` is this thread's polarization view of
-// the group's interleaved exchange array (base + p).
-template <int NP, int E, bool INV, class Bar>
-__device__ __forceinline__ void fft_regs(float2 (&x)[E], const int j, float2* e,
-                                         const float2* __restrict__ tw, Bar bar) {
+// `bar` synchronizes the group (both polarizations); `e1` and `e2` are this thread's polarization
+// views (base + p) of the group's interleaved exchange arrays for the first and the second
+// exchange.  `war` adds the barrier before each store that protects the previous loads of the
+// same array; a caller may drop it when every earlier load of that array is already ordered
+// before the store by another barrier (ping-pong arrays, see the forward chain).
+template <int NP, int E, bool INV, bool TWS = false, class Bar>
+__device__ __forceinline__ void fft_regs(float2 (&x)[E], const int j, float2* e1, float2* e2,
+                                         const float2* __restrict__ tw, Bar bar, bool war) {
     constexpr int NPASS = fft_npasses(NP);
-    fft_pass<NP, E, 0, INV>(x, j, tw);
+    fft_pass<NP, E, 0, INV, TWS>(x, j, tw);
     if constexpr (NPASS > 1) {
+        if (war) bar();
+        fft_store<NP, E, 0>(e1, x, j);
         bar();
-        fft_store<NP, E, 0>(e, x, j);
-        bar();
-        fft_load<NP, E, 1>(e, x, j);
-        fft_pass<NP, E, 1, INV>(x, j, tw);
+        fft_load<NP, E, 1>(e1, x, j);
+        fft_pass<NP, E, 1, INV, TWS>(x, j, tw);
     }
     if constexpr (NPASS > 2) {
+        if (war) bar();
+        fft_store<NP, E, 1>(e2, x, j);
         bar();
-        fft_store<NP, E, 1>(e, x, j);
-        bar();
-        fft_load<NP, E, 2>(e, x, j);
-        fft_pass<NP, E, 2, INV>(x, j, tw);
+        fft_load<NP, E, 2>(e2, x, j);
+        fft_pass<NP, E, 2, INV, TWS>(x, j, tw);
     }
+}
+// The same transform through one exchange array with every barrier.
+template <int NP, int E, bool INV, bool TWS = false, class Bar>
+__device__ __forceinline__ void fft_regs(float2 (&x)[E], const int j, float2* e,
+                                         const float2* __restrict__ tw, Bar bar) {
+    fft_regs<NP, E, INV, TWS>(x, j, e, e, tw, bar, true);
 }
 
 // Slots per thread for a given FFT size: 32 for 2048 points (so 5 subbands x 2 polarizations fit
@@ -336,6 +358,15 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst_smem, const void* src_gm
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+
+// 16-byte asynchronous global -> shared copy (completed by cp_async_wait_all in this thread)
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src_gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)),
+                 "l"(src_gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // named barrier over `count` threads (a multiple of 32)
 __device__ __forceinline__ void named_bar(int id, int count) {

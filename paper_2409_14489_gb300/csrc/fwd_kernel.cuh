@@ -105,7 +105,8 @@ __device__ __forceinline__ int cpad(int k) { return k + (k >> 4); }
 // of w[l][m] row_l[k0 + q - m] (rows swizzled, with circular halo).  NCH > 0 fixes the number
 // of four-tap chunks at compile time: one window of 8 + 4 NCH samples per row then serves all
 // chunks.  NCH = 0 handles any chunk count with one 12-sample window per chunk.
-template <int E, int NCH>
+// WS: the taps `wbase` are in shared memory (plain loads) instead of global memory.
+template <int E, int NCH, bool WS = false>
 __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restrict__ wbase,
                                      const float* __restrict__ rows0, int k0, float (&acc)[8]) {
 #pragma unroll
@@ -117,7 +118,7 @@ __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restric
             const float4* wrow = wbase + l * NCH;
             float4 w4[NCH];
 #pragma unroll
-            for (int c = 0; c < NCH; ++c) w4[c] = __ldg(wrow + c);
+            for (int c = 0; c < NCH; ++c) w4[c] = WS ? wrow[c] : __ldg(wrow + c);
             const int m_lo = m0 - 4 * (NCH - 1);
             float win[8 + 4 * NCH];
 #pragma unroll
@@ -165,18 +166,24 @@ __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restric
 
 // Rotation factors for the 8 samples k = k0 .. k0 + 7 of subband i, step s:
 // theta_i[k] = sum_l sum_m w[s][i][l][m + nc] P_l[k - m]; stores (cos theta, sin theta).
+// `s_taps` is the step's tap buffer in shared memory when a.taps_smem is set.
 template <int E>
 __device__ __forceinline__ void nlpr_rotation8(const ChainArgs& a, const float* __restrict__ prow0,
                                                float2* __restrict__ cs_row,
-                                               const float2* __restrict__ rot_tbl, int s, int i,
+                                               const float2* __restrict__ rot_tbl,
+                                               const float4* __restrict__ s_taps, int s, int i,
                                                int k0) {
-    const float4* wbase = reinterpret_cast<const float4*>(
-        a.taps + (size_t)(s * a.n_sb + i) * a.n_sb * a.ntaps_pad);
     float acc[8];
-    if (a.nchunks == 3) {
-        fir8<E, 3>(a, wbase, prow0, k0, acc);           // 9 to 12 taps
+    if (a.taps_smem) {
+        fir8<E, 3, true>(a, s_taps + i * a.n_sb * 3, prow0, k0, acc);     // 9 to 12 taps
     } else {
-        fir8<E, 0>(a, wbase, prow0, k0, acc);
+        const float4* wbase = reinterpret_cast<const float4*>(
+            a.taps + (size_t)(s * a.n_sb + i) * a.n_sb * a.ntaps_pad);
+        if (a.nchunks == 3) {
+            fir8<E, 3>(a, wbase, prow0, k0, acc);
+        } else {
+            fir8<E, 0>(a, wbase, prow0, k0, acc);
+        }
     }
     float2* dst = cs_row + cpad(k0);                   // k0 % 16 in {0, 8}: no carry below
 #pragma unroll
@@ -212,7 +219,9 @@ __device__ __forceinline__ ThreadPos thread_pos(int n_sb) {
 template <int NP, int ST, bool CKPT = false>
 __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* smem,
                                             int region_bytes, uint64_t* bar_g, uint32_t parity,
-                                            const float2* __restrict__ s_rot, const ThreadPos& tp,
+                                            const float2* __restrict__ s_rot,
+                                            const float2* __restrict__ s_tw,
+                                            float4* __restrict__ s_taps, const ThreadPos& tp,
                                             bool real, int seq, int blk) {
     using S = Storage<ST>;
     using Pol = typename S::Pol;
@@ -222,8 +231,21 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     constexpr int CSL = NP + NP / 16;                  // float2 per (cos, sin) row
     const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
     unsigned char* region = smem + (size_t)g * region_bytes;
-    float2* e = reinterpret_cast<float2*>(region) + gi * XL + p;
+    float2* const grpA = reinterpret_cast<float2*>(region) + gi * XL;   // this group's array A
+    float2* e = grpA + p;
     const GroupBar<NP, E> bar{1 + g * a.n_sb + gi};
+    // Ping-pong layout: a second exchange array B.  Three-pass FFTs exchange through A then B;
+    // two-pass FFTs use A for the inverse and B for the forward transform of a step.  The
+    // (cos, sin) rows then live in the array the inverse FFT read last, which stays idle until
+    // the forward FFT's second exchange (or the next step's inverse FFT).
+    constexpr int NPASS = fft_npasses(NP);
+    const bool pp = a.layout == kLayoutPingPong;
+    float2* const grpB = pp ? reinterpret_cast<float2*>(region + a.exb_off) + gi * XL : grpA;
+    float2* const eB = grpB + p;
+    float2* const inv1 = e;
+    float2* const inv2 = NPASS > 2 ? eB : e;
+    float2* const fwd1 = (NPASS > 2 || !pp) ? e : eB;
+    float2* const fwd2 = eB;
     // Checkpoints for the adjoint (CKPT): per block, n_st + 2 fields of N complex pairs in the
     // slot order [c][gi][idx][p]: c = 0 the spectrum after the first GVD, c = 1 + s the time
     // samples of step s before its rotation, c = n_st + 1 the spectrum after the last GVD.
@@ -299,7 +321,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     __syncthreads();
 
     // ---------------- 2. full-band DFT + DEMUX -------------------------------------------
-    fft_regs<NP, E, false>(x, j, e, a.fft_tw, bar);               // Y_r, r = gi
+    fft_regs<NP, E, false, true>(x, j, e, s_tw, bar);              // Y_r, r = gi
     bar();
 #pragma unroll
     for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = x[t];
@@ -333,17 +355,30 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         for (int t = 0; t < E; ++t) x[t] = c_mul(x[t], __ldg(h + j + TPF * t));
     }
     save_ckpt(0, x);
-    // intensity rows and (cos, sin) rows: after the exchange arrays when they fit (a.sep), else
-    // aliased onto them (then two more block-wide barriers per step guard the reuse)
-    float* prow0 = reinterpret_cast<float*>(region + a.nlpr_off);
-    float2* csbase = reinterpret_cast<float2*>(prow0 + a.n_sb * a.pstride);
-    const float2* cs_mine = csbase + gi * CSL;
+    // intensity rows and (cos, sin) rows: see the kLayout* constants
+    const bool alias = a.layout == kLayoutAlias;
+    float* const prowA = reinterpret_cast<float*>(region + a.nlpr_off);
+    float2* const cs_row = pp ? (NPASS > 2 ? grpB : grpA)
+                              : reinterpret_cast<float2*>(prowA + a.n_sb * a.pstride) + gi * CSL;
+    const bool group_cs_bar = pp && a.pbuf_bytes > 0;
     const int cs_base = (TPF >= 16) ? cpad(j) : 0;
+    const int n4 = a.n_sb * a.n_sb * 3;               // float4 per step's taps (12 per row)
 #pragma unroll 1
     for (int s = 0; s < a.n_st; ++s) {
-        fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);            // subband time samples
+        // stage this step's taps (asynchronous copies, completed before the intensity barrier);
+        // buffer s & 1 was last read in step s - 2, before step s - 1's intensity barrier
+        float4* const taps_buf = s_taps + (s & 1) * n4;
+        if (a.taps_smem) {
+            const float4* src = reinterpret_cast<const float4*>(a.taps) + (size_t)s * n4;
+            for (int k = threadIdx.x; k < n4; k += blockDim.x) cp_async16(taps_buf + k, src + k);
+            cp_async_commit();
+        }
+        fft_regs<NP, E, true, true>(x, j, inv1, inv2, s_tw, bar, !pp); // subband time samples
         save_ckpt(1 + s, x);
-        if (!a.sep) __syncthreads();
+        if (alias) __syncthreads();
+        float* const prow0 =
+            group_cs_bar ? reinterpret_cast<float*>(region + a.nlpr_off + (s & 1) * a.pbuf_bytes)
+                         : prowA;
         {
             float* prow = prow0 + gi * a.pstride;
             const int mb = a.H + a.p_off;
@@ -372,20 +407,28 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                 }
             }
         }
+        if (a.taps_smem) cp_async_wait_all();
         __syncthreads();
 #pragma unroll
         for (int h8 = 0; h8 < E / 16; ++h8)
-            nlpr_rotation8<E>(a, prow0, csbase + gi * CSL, s_rot, s, gi,
+            nlpr_rotation8<E>(a, prow0, cs_row, s_rot, taps_buf, s, gi,
                               E * j + (E / 2) * p + 8 * h8);
-        __syncthreads();
+        // (cos, sin) of subband gi are written and read by group gi only.  With two intensity
+        // buffers nothing else is shared before the next step's intensity barrier: a group that
+        // runs ahead writes the other buffer.
+        if (group_cs_bar) {
+            bar();
+        } else {
+            __syncthreads();
+        }
 #pragma unroll
         for (int t = 0; t < E; ++t) {
-            const float2 rot = (TPF >= 16) ? cs_mine[cs_base + (TPF + TPF / 16) * t]
-                                           : cs_mine[cpad(j + TPF * t)];
+            const float2 rot = (TPF >= 16) ? cs_row[cs_base + (TPF + TPF / 16) * t]
+                                           : cs_row[cpad(j + TPF * t)];
             x[t] = c_mul(x[t], rot);
         }
-        if (!a.sep) __syncthreads();
-        fft_regs<NP, E, false>(x, j, e, a.fft_tw, bar);           // back to subband bins
+        if (alias) __syncthreads();
+        fft_regs<NP, E, false, true>(x, j, fwd1, fwd2, s_tw, bar, !pp);  // back to subband bins
         const float2* h = a.gvd + (size_t)((s < a.n_st - 1 ? 1 : 2) * a.n_sb + gi) * NP;
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = c_mul(x[t], __ldg(h + j + TPF * t));
@@ -418,7 +461,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         }
     }
     __syncthreads();
-    fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);                // x[n_sb n' + r], r = gi
+    fft_regs<NP, E, true, true>(x, j, e, s_tw, bar);               // x[n_sb n' + r], r = gi
     if (real) {
         Pol* dst = reinterpret_cast<Pol*>(a.out) + 2 * (long long)seq * a.L + p;
         const int lo = a.n_ov / 2;
@@ -443,7 +486,11 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
     __shared__ uint64_t bars[kMaxG];
     __shared__ float2 s_rot[kRotTable];
     const ThreadPos tp = thread_pos<NP>(a.n_sb);
+    float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)a.G * a.region_bytes);
+    float4* const s_taps = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_tw) +
+                                                     chain_tw_bytes(fft_tw_size(NP)));
     for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
+    for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(a.fft_tw + k);
     if (tp.tid < a.G) mbar_init(&bars[tp.tid], 1);
     mbar_fence_init();
     __syncthreads();
@@ -452,7 +499,8 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
     const bool real = item < total;
     const int seq = real ? (int)(item / a.n_blocks) : 0;
     const int blk = real ? (int)(item % a.n_blocks) : 0;
-    chain_block<NP, ST>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, tp, real, seq, blk);
+    chain_block<NP, ST>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, s_tw, s_taps, tp, real,
+                        seq, blk);
 }
 
 // Forward launch that also writes the adjoint's checkpoints (complex64 storage).
@@ -462,7 +510,11 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_ckpt_kernel(const ChainArg
     __shared__ uint64_t bars[kMaxG];
     __shared__ float2 s_rot[kRotTable];
     const ThreadPos tp = thread_pos<NP>(a.n_sb);
+    float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)a.G * a.region_bytes);
+    float4* const s_taps = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_tw) +
+                                                     chain_tw_bytes(fft_tw_size(NP)));
     for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
+    for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(a.fft_tw + k);
     if (tp.tid < a.G) mbar_init(&bars[tp.tid], 1);
     mbar_fence_init();
     __syncthreads();
@@ -471,7 +523,8 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_ckpt_kernel(const ChainArg
     const bool real = item < total;
     const int seq = real ? (int)(item / a.n_blocks) : 0;
     const int blk = real ? (int)(item % a.n_blocks) : 0;
-    chain_block<NP, 0, true>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, tp, real, seq, blk);
+    chain_block<NP, 0, true>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, s_tw, s_taps, tp,
+                             real, seq, blk);
 }
 
 // Persistent form for a batch of jobs that share N', the subband count and the storage type:
@@ -488,6 +541,13 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_persistent_kernel(
     __shared__ ChainArgs s_job;
     __shared__ int s_item;
     const ThreadPos tp = thread_pos<NP>(n_sb);
+    float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)G * region_bytes);
+    float4* const s_taps = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_tw) +
+                                                     chain_tw_bytes(fft_tw_size(NP)));
+    {   // every job of the launch has this N', so any job's twiddle table will do
+        const float2* tw = jobs[items[0].x].fft_tw;
+        for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(tw + k);
+    }
     if (tp.tid < G) mbar_init(&bars[tp.tid], 1);
     mbar_fence_init();
     int rot_of = -1;                               // job whose rotation table is in s_rot
@@ -507,8 +567,8 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_persistent_kernel(
         }
         const int blk = w.y + tp.g;
         const bool real = blk < s_job.n_blocks;
-        if (!chain_block<NP, ST>(s_job, smem, region_bytes, &bars[tp.g], it & 1u, s_rot, tp, real,
-                                 0, real ? blk : 0))
+        if (!chain_block<NP, ST>(s_job, smem, region_bytes, &bars[tp.g], it & 1u, s_rot, s_tw,
+                                 s_taps, tp, real, 0, real ? blk : 0))
             return;
         __syncthreads();                               // s_item / s_job reuse
     }
@@ -520,7 +580,7 @@ cudaError_t fwd_launch(const ChainArgs& a, int threads, cudaStream_t stream) {
     const long long total = (long long)a.batch * a.n_blocks;
     const long long grid = (total + a.G - 1) / a.G;
     if (grid <= 0) return cudaSuccess;
-    const size_t smem = (size_t)a.G * a.region_bytes;
+    const size_t smem = (size_t)a.G * a.region_bytes + a.tbl_bytes;
     cbessfm_fwd_kernel<NP, ST><<<(unsigned)grid, threads, smem, stream>>>(a);
     return cudaGetLastError();
 }
@@ -537,9 +597,9 @@ cudaError_t fwd_prepare(int smem_bytes) {
 template <int NP, int ST>
 cudaError_t fwd_persistent_launch(const ChainArgs* jobs, const int2* items, int n_items,
                                   unsigned int* counter, int n_sb, int G, int region_bytes,
-                                  int threads, int grid, cudaStream_t stream) {
+                                  int tbl_bytes, int threads, int grid, cudaStream_t stream) {
     if (n_items <= 0 || grid <= 0) return cudaSuccess;
-    const size_t smem = (size_t)G * region_bytes;
+    const size_t smem = (size_t)G * region_bytes + tbl_bytes;
     cbessfm_fwd_persistent_kernel<NP, ST><<<grid, threads, smem, stream>>>(
         jobs, items, n_items, counter, n_sb, G, region_bytes);
     return cudaGetLastError();

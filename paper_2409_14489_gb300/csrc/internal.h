@@ -8,6 +8,18 @@
 
 namespace cbessfm {
 
+// Shared-memory layouts of one OLS block's region in the forward chain.
+//  kLayoutAlias:    one exchange array; the intensity and (cos, sin) rows alias it, so two more
+//                   block-wide barriers per step guard the reuse.
+//  kLayoutSeparate: one exchange array, then the intensity rows and the (cos, sin) rows.
+//  kLayoutPingPong: two exchange arrays A and B used alternately by the FFT passes (no barrier
+//                   before a store), the (cos, sin) rows inside the array the inverse FFT read
+//                   last, then one or two intensity-row buffers.  With two buffers (pbuf_bytes >
+//                   0) the barrier after the FIR covers only the subband group.
+constexpr int kLayoutAlias = 0;
+constexpr int kLayoutSeparate = 1;
+constexpr int kLayoutPingPong = 2;
+
 // Kernel arguments of the chain kernels (forward and adjoint share them).
 struct ChainArgs {
     const void* in;              // [batch][L] samples (storage type of the plan)
@@ -20,8 +32,12 @@ struct ChainArgs {
     int nc, ntaps_pad, nchunks;  // FIR: N_c, taps per row (multiple of 4), chunks of 4 taps
     int H, p_off, pstride;       // FIR intensity buffer: halo, alignment offset, row stride
     int region_bytes;            // shared memory per OLS block
-    int nlpr_off;                // byte offset of the intensity / (cos, sin) rows in the region
-    int sep;                     // 1 if those rows do not alias the exchange arrays
+    int nlpr_off;                // byte offset of the intensity rows in the region
+    int layout;                  // shared-memory layout of a block's region (kLayout*)
+    int exb_off;                 // byte offset of the second exchange array (ping-pong layout)
+    int pbuf_bytes;              // bytes from the first to the second intensity-row buffer, or 0
+    int tbl_bytes;               // shared memory after the G regions: FFT twiddles (+ tap buffers)
+    int taps_smem;               // 1: each step's taps are staged in shared memory (4-tap chunks = 3)
     const float2* gvd;           // [3][n_sb][NP]: first (x 1/N), interior (x 1/NP), last (x 1/NP)
     const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
     const float2* fft_tw;        // FFT pass twiddles (fft_tw_size(NP))
@@ -44,7 +60,8 @@ struct PlanImpl {
     cbessfm_storage storage = CBESSFM_C64;
     int N = 16, n_ov = 0, V = 16;
     int nc = 0, ntaps_pad = 4, nchunks = 1, H = 4, p_off = 3, pstride = 32;
-    int region_bytes = 0, nlpr_off = 0, sep = 0, G = 1, threads = 0;
+    int region_bytes = 0, nlpr_off = 0, layout = 0, exb_off = 0, pbuf_bytes = 0, G = 1, threads = 0;
+    int tbl_bytes = 0, taps_smem = 0;
     double step_length = 0.0;
     float2* d_gvd = nullptr;      // [3][n_sb][NP]
     float* d_kdisp = nullptr;     // [n_sb][NP] 2 pi^2 beta2 L_step f^2 (ratio derivative)
@@ -73,8 +90,17 @@ ChainArgs make_chain_args(const PlanImpl& p);
 constexpr int kMaxDynSmem = 224 * 1024;     // 227 KB per block minus room for static shared memory
 constexpr int kMaxThreads = 640;
 constexpr int kMaxG = 16;
-// OLS blocks per CTA for a block of `tb` threads and `region_bytes` of shared memory (0 = none fits).
-int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands);
+// OLS blocks per CTA for a block of `tb` threads and `region_bytes` of shared memory, with
+// `extra_bytes` more per CTA (0 = none fits).
+int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands, int extra_bytes = 0);
+
+// Per-CTA shared tables of the forward chain, after the G block regions: the FFT pass twiddles of
+// N' (rounded to 128 bytes), then, when taps are staged, two buffers of one step's taps
+// ([bands][bands][12] floats each).
+__host__ __device__ constexpr int chain_tw_bytes(int tw_entries) {
+    return (8 * tw_entries + 127) / 128 * 128;
+}
+__host__ __device__ constexpr int chain_taps_bytes(int bands) { return 2 * bands * bands * 12 * 4; }
 
 // Error reporting (thread-local message, see cbessfm_last_error).
 cbessfm_status fail(cbessfm_status st, const char* fmt, ...);
@@ -88,7 +114,8 @@ const PlanImpl* plan_impl(const cbessfm_plan* plan);
 // Persistent batched launch of the forward kernel for one (NP, storage) group.
 cudaError_t launch_forward_persistent(int np, int storage, const ChainArgs* jobs, const int2* items,
                                       int n_items, unsigned int* counter, int n_sb, int G,
-                                      int region_bytes, int threads, int grid, cudaStream_t stream);
+                                      int region_bytes, int tbl_bytes, int threads, int grid,
+                                      cudaStream_t stream);
 cudaError_t forward_persistent_occupancy(int np, int storage, int threads, int smem_bytes,
                                          int* ctas_per_sm);
 

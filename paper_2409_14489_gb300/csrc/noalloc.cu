@@ -50,6 +50,10 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_noalloc_kernel(
     __shared__ ChainArgs s_job;
     __shared__ int s_item;
     const ThreadPos tp = thread_pos<NP>(n_sb);
+    float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)G * region_bytes);
+    float4* const s_taps = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_tw) +
+                                                     chain_tw_bytes(fft_tw_size(NP)));
+    for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(jobs[0].fft_tw + k);
     if (tp.tid < G) mbar_init(&bars[tp.tid], 1);
     mbar_fence_init();
     const int n_items = prefix[njobs];
@@ -71,8 +75,8 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_noalloc_kernel(
         }
         const int blk = (item - prefix[k]) * G + tp.g;
         const bool real = blk < s_job.n_blocks;
-        if (!chain_block<NP, 0>(s_job, smem, region_bytes, &bars[tp.g], it & 1u, s_rot, tp, real,
-                                0, real ? blk : 0))
+        if (!chain_block<NP, 0>(s_job, smem, region_bytes, &bars[tp.g], it & 1u, s_rot, s_tw,
+                                s_taps, tp, real, 0, real ? blk : 0))
             return;
         __syncthreads();
     }
@@ -94,9 +98,9 @@ cudaError_t noalloc_prepare_all() {
 }
 
 cudaError_t noalloc_launch(int np, const ChainArgs* jobs, const int* prefix, int njobs,
-                           unsigned int* counter, int n_sb, int G, int region_bytes, int threads,
-                           int grid, cudaStream_t st) {
-    const size_t smem = (size_t)G * region_bytes;
+                           unsigned int* counter, int n_sb, int G, int region_bytes, int tbl_bytes,
+                           int threads, int grid, cudaStream_t st) {
+    const size_t smem = (size_t)G * region_bytes + tbl_bytes;
 #define CB_CASE(NP)                                                                           \
     case NP:                                                                                  \
         cbessfm_fwd_noalloc_kernel<NP><<<grid, threads, smem, st>>>(jobs, prefix, njobs, counter, \
@@ -175,6 +179,7 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
     int order[kNoallocMaxJobs];
     int prefix[kNoallocMaxJobs + 1];
     int np = 0, n_sb = 0, region = 0;
+    bool any_taps = false;
     for (int k = 0; k < njobs; ++k) {
         const cbessfm_job& jb = jobs[k];
         const PlanImpl* p = plan_impl(jb.plan);
@@ -204,11 +209,19 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
         desc[k].batch = 1;
         desc[k].n_blocks = (int)nb;
         region = std::max(region, p->region_bytes);
+        any_taps = any_taps || desc[k].taps_smem;
         order[k] = k;
     }
     const int tpf = np / fft_slots(np);
     const int tb = 2 * n_sb * tpf;
-    const int G = choose_blocks_per_cta(tb, region, tpf, n_sb);
+    // per-CTA tables after the block regions: twiddles, plus tap buffers when they fit
+    const int tw = chain_tw_bytes(fft_tw_size(np));
+    int tbl = tw + (any_taps ? chain_taps_bytes(n_sb) : 0);
+    int G = choose_blocks_per_cta(tb, region, tpf, n_sb, tbl);
+    if (G < 1 && any_taps) {
+        tbl = tw;
+        G = choose_blocks_per_cta(tb, region, tpf, n_sb, tbl);
+    }
     if (G < 1) return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape for n_fft %d, bands %d", np, n_sb);
     // longest processing time first: order jobs by decreasing cost per work item (insertion
     // sort, stable, no temporary buffer)
@@ -227,6 +240,8 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
         sorted[k] = desc[order[k]];
         sorted[k].G = G;
         sorted[k].region_bytes = region;
+        sorted[k].tbl_bytes = tbl;
+        if (tbl == tw) sorted[k].taps_smem = 0;
         const long long n = prefix[k] + (long long)(sorted[k].n_blocks + G - 1) / G;
         if (n > (1ll << 30)) return fail(CBESSFM_ERR_UNSUPPORTED, "too many work items");
         prefix[k + 1] = (int)n;
@@ -241,7 +256,7 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
     const cbessfm_status st0 = device_setup(dev, &scratch, &n_sm);
     if (st0 != CBESSFM_OK) return st0;
     int per_sm = 0;
-    e = noalloc_occupancy(np, G * tb, G * region, &per_sm);
+    e = noalloc_occupancy(np, G * tb, G * region + tbl, &per_sm);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy");
     if (per_sm < 1) return fail(CBESSFM_ERR_UNSUPPORTED, "kernel does not fit an SM");
     const int grid = (int)std::min<long long>((long long)per_sm * n_sm, prefix[njobs]);
@@ -257,7 +272,8 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
         e = cudaMemcpyAsync(d_prefix, prefix, sizeof(int) * (njobs + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess)
-        e = noalloc_launch(np, d_desc, d_prefix, njobs, d_counter, n_sb, G, region, G * tb, grid, st);
+        e = noalloc_launch(np, d_desc, d_prefix, njobs, d_counter, n_sb, G, region, tbl, G * tb,
+                           grid, st);
     if (e != cudaSuccess) return cuda_fail(e, "no-allocation batched launch");
     return CBESSFM_OK;
 }

@@ -58,6 +58,39 @@ def test_forward_matches_oracle_small(case):
     assert plan.status() == 0
 
 
+LAYOUT_CASES = [
+    Case(1, 16, 4, 3, 3, 0.5, 5 * 12 + 7),                       # one-pass FFT
+    Case(3, 64, 16, 3, 7, 0.12, 4 * 144 + 13, sample_rate=192e9),  # two-pass FFT
+    Case(1, 256, 64, 2, 5, 0.5, 3000, batch=2),                   # several blocks per CTA
+    Case(5, 1024, 256, 3, 11, 0.3, 2 * 3840 + 1001, sample_rate=640e9),
+    Case(2, 2048, 512, 2, 11, 0.3, 4096 + 4000, sample_rate=256e9, seed=4),
+]
+
+
+@pytest.mark.parametrize("case", LAYOUT_CASES, ids=lambda c: f"sb{c.n_sb}_np{c.n_fft}_st{c.n_st}")
+def test_shared_memory_layouts_agree_bitwise(case, monkeypatch):
+    """Every shared-memory layout of the forward chain (ping-pong exchange arrays with two or one
+    intensity buffers, separate rows, rows aliased onto the exchange array) runs the same
+    arithmetic, so the outputs must be identical; the default one also meets the oracle."""
+    taps = case_taps(case)
+    field = random_field(case)
+    outs = {}
+    for lay in ("pingpong2", "pingpong1", "separate", "alias", None):
+        if lay is None:
+            monkeypatch.delenv("CBESSFM_SMEM_LAYOUT", raising=False)
+        else:
+            monkeypatch.setenv("CBESSFM_SMEM_LAYOUT", lay)
+        plan = make_plan(case, taps)
+        outs[lay] = run_gpu(plan, field)
+        assert plan.status() == 0
+    for lay, got in outs.items():
+        assert np.array_equal(got, outs[None]), lay
+    p = oracle_params(case, taps.astype(np.float32).astype(np.float64))
+    want = odbp.dbp_mode_b(field[0].astype(np.complex64).astype(np.complex128), p, case.n_fft,
+                           case.overlap)
+    assert rel_l2(outs[None][0], want, f"layouts/{case}") <= TOL
+
+
 def test_c1_channel_output_parity_and_snr():
     wl = configs.get_workload("c1_tiny")
     lk, sig, d = wl.link, wl.signal, wl.dbp
