@@ -127,8 +127,8 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
  * complex64 storage only.
  *
  * cbessfm_grad_workspace_size -- bytes of device workspace (caller-allocated, 256-byte aligned)
- *   holding, per overlap-and-save block, n_steps + 2 checkpoints of the block's field and the
- *   per-block partial gradients.
+ *   holding, per overlap-and-save block, n_steps + 2 checkpoints of the block's field, two
+ *   block-sized scratch fields of the adjoint and the per-block partial gradients.
  */
 cbessfm_status cbessfm_grad_workspace_size(const cbessfm_plan* plan, int64_t n_samples, int batch,
                                            size_t* bytes);
@@ -151,7 +151,10 @@ cbessfm_status cbessfm_backpropagate_checkpointed(const cbessfm_plan* plan, cons
  *   grad_ratio   device double scalar dL/drho, or NULL.
  *   grad_in      device [batch][n_samples] G of the input (overwritten), or NULL.
  * Per block the adjoint walks the steps backwards: conjugate GVD, inverse transforms, and the
- * adjoint of the rotation, the coupled-band FIR (transposed taps) and the intensity.
+ * adjoint of the rotation, the coupled-band FIR (transposed taps) and the intensity.  dL/drho
+ * (the ratio enters only the first and the last GVD, Sec. III-C) is accumulated as one term per
+ * step built from exp(j theta) - 1, which keeps its FP32 error at the level of the other
+ * gradients on long links where the two end terms nearly cancel.
  */
 cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, double* grad_coeffs,
                             double* grad_ratio, void* grad_in, void* workspace, size_t ws_bytes,

@@ -35,8 +35,10 @@ class CBESSFMFunction(torch.autograd.Function):
         module = ctx.module
         batch, L = cbessfm.Plan._shape(gy)
         ws = module.workspace(L, batch)
-        gc, gr, gi = module.plan.grad(gy.contiguous(), ws, want_input=ctx.needs_input_grad[0])
-        return gi, gc.to(ctx.taps_dtype), gr.to(ctx.ratio_dtype), None
+        gc, gr, gi = module.plan.grad(gy.contiguous(), ws, want_input=ctx.needs_input_grad[0],
+                                      want_ratio=ctx.needs_input_grad[2])
+        return (gi, gc.to(ctx.taps_dtype), gr.to(ctx.ratio_dtype) if gr is not None else None,
+                None)
 
 
 class CBESSFM(torch.nn.Module):

@@ -215,9 +215,11 @@ class Plan:
             workspace.numel(), _stream_handle(stream)))
         return out
 
-    def grad(self, grad_out, workspace, want_input: bool = True, stream=None):
+    def grad(self, grad_out, workspace, want_input: bool = True, want_ratio: bool = True,
+             stream=None):
         """Adjoint of the last checkpointed forward: returns (dL/dtaps [steps, bands, bands,
-        ntaps] float64, dL/dratio float64 scalar, dL/din complex64 or None)."""
+        ntaps] float64, dL/dratio float64 scalar or None, dL/din complex64 or None).  Leaving
+        out the ratio gradient skips its per-step work in the adjoint kernel."""
         import torch
         if not (grad_out.is_cuda and grad_out.dtype == torch.complex64):
             raise ValueError("grad_out must be a complex64 CUDA tensor")
@@ -225,10 +227,11 @@ class Plan:
         batch, L = self._shape(g)
         gc = torch.zeros((max(self.steps, 0), self.bands, self.bands, self.ntaps),
                          dtype=torch.float64, device="cuda")
-        gr = torch.zeros((), dtype=torch.float64, device="cuda")
+        gr = torch.zeros((), dtype=torch.float64, device="cuda") if want_ratio else None
         gi = torch.empty_like(g) if want_input else None
         _check(_lib.cbessfm_grad(self._h, g.data_ptr(), gc.data_ptr() if gc.numel() else None,
-                                 gr.data_ptr(), gi.data_ptr() if gi is not None else None,
+                                 gr.data_ptr() if gr is not None else None,
+                                 gi.data_ptr() if gi is not None else None,
                                  workspace.data_ptr(), workspace.numel(), L, batch,
                                  _stream_handle(stream)))
         return gc, gr, gi

@@ -44,6 +44,20 @@ __device__ __forceinline__ void fir8_acc(const ChainArgs& a, const float4* __res
     }
 }
 
+// Read-only load that the compiler may not merge with another load of the same address (keeping
+// a table value live across a whole step costs registers that the step needs).
+__device__ __forceinline__ float ldg_once(const float* p) {
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float2 ldg2_once(const float2* p) {
+    float2 v;
+    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+
 // write value v of row sample n (and its circular halo copies) into swizzled row `row`
 template <int NP, int E>
 __device__ __forceinline__ void row_store(float* row, int mb, int n, int H, float v) {
@@ -133,28 +147,39 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     __syncthreads();
     // x now holds G for the spectrum after the last GVD.
     const float* kd = a.kdisp + (size_t)gi * NP;
-    // the ratio terms cancel strongly across bins: accumulate them in FP64
+    // Splitting-ratio gradient.  With Q(Z) = sum_bins kdisp Im(conj(G_Z) Z), the ratio enters
+    // the first and the last GVD only, so dL/drho = Q(Z_0) - Q(Z_N) (Z_s: spectrum entering step
+    // s, Z_N the final one).  Q is unchanged by a GVD, so the difference telescopes into one
+    // term per step: Q(Z_s) - Q(W_s), W_s the spectrum leaving the rotation.  With
+    // psi = exp(j theta) - 1, D_Z = DFT(psi u) and D_G = DFT(conj(psi) G_v + 2 G_P u),
+    //   Q(Z_s) - Q(W_s) = sum kdisp Im(conj(D_G) Z_s - conj(G_W) D_Z),
+    // where D_Z and D_G come from their own small sources.  On long links the two end terms
+    // are thousands of times the result, and their FP32 rounding would dominate it.  Z_s is
+    // rebuilt backwards, Z_s = NP conj(h_s) Z_(s+1) - D_Z / NP (|h_s| = 1/NP), from the final
+    // spectrum, and the adjoint's own G for Z_s becomes NP G_W + D_G.  kdisp omits the
+    // subband-centre part (an exact invariant), which also keeps the two terms of a step from
+    // cancelling when theta is large.  Each thread sums its 16 bins of a term in FP32 (those
+    // rounding errors are independent across threads and steps) and adds the partial to an
+    // FP64 total once per term; GB300's FP64 rate makes per-bin FP64 arithmetic costly.
     double rho_part = 0.0;
-    if (a.n_st > 0) {
-        // d(T_last)/d(rho) = +j kdisp T_last  ->  Re(conj(G) j kdisp X) = -kdisp Im(conj(G) X)
-        float2 xf[E];
-        load_ckpt(a.n_st + 1, xf);
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const float im = x[t].x * xf[t].y - x[t].y * xf[t].x;      // Im(conj(G) X)
-            rho_part -= (double)__ldg(kd + j + TPF * t) * (double)im;
-        }
-    }
+    const float NPf = (float)NP;
+    const float inv_NP = 1.0f / NPf;
+    float2* const sg = a.stash + (size_t)gblk * 4 * N + (size_t)gi * NP * 2 + p;   // G_W
+    float2* const sz = sg + 2 * N;                                               // Z_s
 
     // ---- 2. steps, last to first ----------------------------------------------------------
-    float2* cs_mine = csbase + gi * CSL;
+    float2* cs_mine = csbase + gi * CSL;                                    // psi rows
     const int k0 = E * j + (E / 2) * p;                                    // FIR outputs k0 ..
 #pragma unroll 1
     for (int s = a.n_st - 1; s >= 0; --s) {
         const float2* h = a.gvd + (size_t)((s < a.n_st - 1 ? 1 : 2) * n_sb + gi) * NP;
+        // G_W = conj(h) G_(Z_(s+1)), kept in the block's scratch when dL/drho is wanted
+        const bool rho = a.want_ratio != 0;
 #pragma unroll
-        for (int t = 0; t < E; ++t) x[t] = c_mulc(x[t], __ldg(h + j + TPF * t));   // conj(T) G
-        fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);                         // G_v
+        for (int t = 0; t < E; ++t) {
+            x[t] = c_mulc(x[t], __ldg(h + j + TPF * t));
+            if (real && rho) sg[2 * (j + TPF * t)] = x[t];
+        }
         {
             float2 u[E];
             load_ckpt(1 + s, u);
@@ -176,26 +201,58 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
                 fir8_acc<E>(a, wb, prow0, k0 + 8 * h8, acc);
                 float2* dst = cs_mine + cpad(k0 + 8 * h8);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = rotation_factor(acc[q], s_rot);
+                for (int q = 0; q < 8; ++q) dst[q] = rotation_psi(acc[q], s_rot);
             }
         }
         __syncthreads();
+        // Two inverse transforms share one call site: D_Z = conj(IDFT(conj(psi u))), then G_v.
+        // Between them: Z_s = NP conj(h) Z_(s+1) - D_Z / NP, the G_W part of the ratio term, and
+        // G_W back into x as the second transform's input.
         {
-            // G_theta and the first part of G_u
+            const float2* z1 = s == a.n_st - 1 ? ck + (size_t)(a.n_st + 1) * 2 * N : sz;
+#pragma unroll 1
+            for (int ph = rho ? 0 : 1; ph < 2; ++ph) {
+                if (ph == 0) {
+                    float2 u[E];
+                    load_ckpt(1 + s, u);
+#pragma unroll
+                    for (int t = 0; t < E; ++t) x[t] = c_conj(c_mul(cs_mine[cpad(j + TPF * t)], u[t]));
+                }
+                fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);
+                if (ph == 0) {
+                    float rs = 0.f;
+#pragma unroll
+                    for (int t = 0; t < E; ++t) {
+                        const int o = 2 * (j + TPF * t);
+                        const float2 dz = c_conj(x[t]);
+                        const float2 hv = ldg2_once(h + j + TPF * t);
+                        const float2 zs = c_sub(c_scale(c_mulc(z1[o], hv), NPf), c_scale(dz, inv_NP));
+                        if (real) sz[o] = zs;
+                        const float2 gw = sg[o];
+                        rs = fmaf(-ldg_once(kd + j + TPF * t), gw.x * dz.y - gw.y * dz.x, rs);
+                        x[t] = gw;
+                    }
+                    rho_part += (double)rs;
+                }
+            }
+        }
+        {
+            // G_theta and the first part of D_G's source, conj(psi) G_v
             float2 u[E];
             load_ckpt(1 + s, u);
             float* trow = trow0 + gi * a.pstride;
 #pragma unroll
             for (int t = 0; t < E; ++t) {
-                const float2 cs = cs_mine[cpad(j + TPF * t)];
-                const float2 v = c_mul(u[t], cs);
+                const float2 ps = cs_mine[cpad(j + TPF * t)];
+                const float2 v = c_mul(u[t], make_float2(1.0f + ps.x, ps.y));
                 float gt = -(x[t].x * v.y - x[t].y * v.x);                 // -Im(conj(G_v) v)
                 gt += __shfl_xor_sync(0xffffffffu, gt, 1);
                 if (p == 0) {
                     row_store<NP, E>(trow, mb, j + TPF * t, a.H, gt);
                     gtplain[gi * NP + j + TPF * t] = gt;
                 }
-                x[t] = c_mulc(x[t], cs);                                    // exp(-j theta) G_v
+                // conj(psi) G_v (the ratio path adds G_v back in the spectral domain as NP G_W)
+                x[t] = rho ? c_mulc(x[t], ps) : c_mulc(x[t], make_float2(1.0f + ps.x, ps.y));
             }
         }
         __syncthreads();
@@ -315,20 +372,23 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
         }
         __syncthreads();
         for (int k = rem; k < n_acc; k += TB) accw[k] = 0.f;
-        fft_regs<NP, E, false>(x, j, e, a.fft_tw, bar);                        // G for X_s
-    }
-
-    // ---- 3. first GVD, ratio term, adjoint of entry (MUX + IDFT_N), scatter to G_in ------
-    if (a.n_st > 0) {
-        // d(T_first)/d(rho) = -j kdisp T_first  ->  +kdisp Im(conj(G) X_0)
-        float2 x0[E];
-        load_ckpt(0, x0);
+        // D_G = DFT(conj(psi) G_v + 2 G_P u); G for Z_s = NP G_W + D_G; the D_G part of the ratio
+        fft_regs<NP, E, false>(x, j, e, a.fft_tw, bar);
+        if (rho) {
+            float rs = 0.f;
 #pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const float im = x[t].x * x0[t].y - x[t].y * x0[t].x;
-            rho_part += (double)__ldg(kd + j + TPF * t) * (double)im;
+            for (int t = 0; t < E; ++t) {
+                const int o = 2 * (j + TPF * t);
+                const float2 zs = sz[o];
+                rs = fmaf(ldg_once(kd + j + TPF * t), x[t].x * zs.y - x[t].y * zs.x, rs);
+                const float2 gw = sg[o];
+                x[t] = make_float2(fmaf(NPf, gw.x, x[t].x), fmaf(NPf, gw.y, x[t].y));
+            }
+            rho_part += (double)rs;
         }
     }
+
+    // ---- 3. first GVD, adjoint of entry (MUX + IDFT_N), scatter to G_in ---------------------
     atomicAdd(acc_rho, rho_part);                 // warps may span several small blocks
     {
         const float2* h = a.gvd + (size_t)gi * NP;
@@ -479,8 +539,10 @@ int adj_region_bytes(const PlanImpl& p) {
     return round_up_i(bytes, 128);
 }
 
+// Workspace: checkpoints | adjoint scratch (two fields per block) | per-block partial
+// gradients | FP64 sums.
 struct Layout {
-    size_t ckpt_bytes, part_bytes, padded_bytes, total;
+    size_t ckpt_bytes, stash_bytes, part_bytes, padded_bytes, total;
     long long n_blk;
     int part_stride;
 };
@@ -490,12 +552,14 @@ Layout layout(const PlanImpl& p, long long n_samples, int batch) {
     const long long nb = (n_samples + p.V - 1) / p.V;
     l.n_blk = nb * batch;
     l.ckpt_bytes = (size_t)l.n_blk * (size_t)(p.n_st + 2) * 16 * p.N;
+    l.stash_bytes = p.n_st > 0 ? (size_t)l.n_blk * 2 * 16 * p.N : 0;
     l.part_stride = p.n_st * p.n_sb * p.n_sb * p.ntaps_pad + 4;
     l.part_bytes = (size_t)l.n_blk * l.part_stride * sizeof(float);
     l.padded_bytes = ((size_t)l.part_stride * sizeof(double) + 255) / 256 * 256;
     l.ckpt_bytes = (l.ckpt_bytes + 255) / 256 * 256;
+    l.stash_bytes = (l.stash_bytes + 255) / 256 * 256;
     l.part_bytes = (l.part_bytes + 255) / 256 * 256;
-    l.total = l.ckpt_bytes + l.part_bytes + l.padded_bytes;
+    l.total = l.ckpt_bytes + l.stash_bytes + l.part_bytes + l.padded_bytes;
     return l;
 }
 
@@ -582,10 +646,12 @@ cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, doub
     a.batch = batch;
     a.n_blocks = (int)((n_samples + p->V - 1) / p->V);
     a.ckpt = reinterpret_cast<float2*>(ws);
-    a.gpart = reinterpret_cast<float*>(ws + l.ckpt_bytes);
+    a.stash = reinterpret_cast<float2*>(ws + l.ckpt_bytes);
+    a.gpart = reinterpret_cast<float*>(ws + l.ckpt_bytes + l.stash_bytes);
     a.gout = static_cast<const float2*>(grad_out);
     a.gin = static_cast<float2*>(grad_in);
     a.kdisp = p->d_kdisp;
+    a.want_ratio = grad_ratio != nullptr ? 1 : 0;
     a.taps_t = p->d_taps_t;
     // the adjoint's own region and CTA shape
     a.region_bytes = adj_region_bytes(*p);
@@ -600,7 +666,7 @@ cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, doub
     if (e == cudaSuccess) e = dispatch<true>(p->n_fft, a, a.G * tb, cs);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint launch");
     const int n_coeffs = p->n_st * p->n_sb * p->n_sb * p->ntaps_pad;
-    double* padded = reinterpret_cast<double*>(ws + l.ckpt_bytes + l.part_bytes);
+    double* padded = reinterpret_cast<double*>(ws + l.ckpt_bytes + l.stash_bytes + l.part_bytes);
     // padded[0 .. n_coeffs) = tap sums, padded[n_coeffs] = ratio sum
     reduce_blocks_kernel<<<(n_coeffs + 1 + 255) / 256, 256, 0, cs>>>(
         a.gpart, l.n_blk, l.part_stride, n_coeffs, padded, padded + n_coeffs);

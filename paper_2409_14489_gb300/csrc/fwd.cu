@@ -29,8 +29,14 @@ __global__ void build_gvd_kernel(float2* __restrict__ gvd, float* __restrict__ k
     sincospi(2.0 * frac, &sn, &cs);
     const double sc = tbl == 0 ? scale0 : scale12;
     gvd[idx] = make_float2((float)(cs * sc), (float)(sn * sc));
-    if (tbl == 0 && kdisp != nullptr)
-        kdisp[r] = (float)(2.0 * 9.86960440108935861883 * beta2 * step_len * f * f);
+    // d(phase)/d(ratio) weight of the splitting-ratio gradient, less the subband-centre part:
+    // a constant per subband multiplies Im<G_i, Z_i>, which every step leaves unchanged (the
+    // chain commutes with a phase rotation of one subband), so it cancels exactly in the
+    // gradient and only adds rounding error.
+    if (tbl == 0 && kdisp != nullptr) {
+        const double fc = (double)(-N / 2 + (long long)i * np + np / 2) * rate / (double)N;
+        kdisp[r] = (float)(2.0 * 9.86960440108935861883 * beta2 * step_len * (f * f - fc * fc));
+    }
 }
 
 cudaError_t launch_build_gvd(const PlanImpl& p, cudaStream_t stream) {

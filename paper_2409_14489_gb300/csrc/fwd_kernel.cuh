@@ -42,6 +42,17 @@ __device__ __forceinline__ float2 rotation_factor(float th, const float2* __rest
     const float d2 = d * d;
     return c_mul(t, make_float2(fmaf(-0.5f, d2, 1.0f), d * fmaf(-0.16666666666666667f, d2, 1.0f)));
 }
+// exp(j theta) - 1 from the same reduction, without cancellation for small theta:
+// t (1 + r1) - 1 = t r1 + (t - 1) with r1 = -d^2/2 + j d (1 - d^2/6) the residual minus one.
+__device__ __forceinline__ float2 rotation_psi(float th, const float2* __restrict__ tbl) {
+    const float kf = rintf(th * kRotInvStep);
+    float d = fmaf(-kf, kRotStepHi, th);
+    d = fmaf(-kf, kRotStepLo, d);
+    const float2 t = tbl[(int)kf & (kRotTable - 1)];
+    const float d2 = d * d;
+    const float2 tr = c_mul(t, make_float2(-0.5f * d2, d * fmaf(-0.16666666666666667f, d2, 1.0f)));
+    return make_float2(tr.x + (t.x - 1.0f), tr.y + t.y);
+}
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: never reached by a live copy
 
 // Barrier over the 2 NP/E threads (both polarizations) of one FFT group.  Groups of a warp or

@@ -18,10 +18,9 @@ GTOL = 1e-4
 # dL/drho is the small difference of a first-GVD and a last-GVD term that cancel exactly in a
 # linear chain (moving dispersion between the two ends changes nothing without the NLPR).  On
 # the 15-step, 5-subband workload the two terms are about 1900 times the difference (oracle,
-# one block: +0.8082 and -0.8086 for a sum of -4.3e-4), so the FP32 rounding of the fields
-# (~1e-7) leaves about 2e-4 relative error in the ratio gradient; the bound below covers that.
-# The tap and input gradients have no such cancellation and meet GTOL.
-RATIO_TOL_LONG = 1e-3
+# one block: +0.8082 and -0.8086 for a sum of -4.3e-4); formed from FP32 fields they would
+# leave about 2e-4 relative error.  The kernel sums one term per step built from
+# exp(j theta) - 1 instead, so the ratio gradient meets GTOL like the others.
 
 CASES = [
     Case(1, 64, 16, 1, 3, 0.5, 4 * 48 + 5, seed=1),
@@ -65,6 +64,29 @@ def test_adjoint_matches_oracle_adjoint(case):
     assert abs(gr - o_ratio) <= GTOL * max(abs(o_ratio), 1e-3 * np.linalg.norm(o_taps)), (gr, o_ratio)
     rel_l2(np.array([gr]), np.array([o_ratio]), f"adjoint/ratio/{case}")
     assert rel_l2(gi, o_in, f"adjoint/input/{case}") <= GTOL
+
+
+def test_tap_gradient_without_ratio_gradient():
+    """Leaving out dL/drho skips its per-step work; the tap and input gradients still match the
+    oracle (the G recursion is then formed directly from the rotated adjoint)."""
+    case = CASES[4]
+    taps = case_taps(case).astype(np.float32).astype(np.float64)
+    field = random_field(case).astype(np.complex64).astype(np.complex128)
+    rng = np.random.default_rng(case.seed + 100)
+    target = (rng.standard_normal(field.shape) + 1j * rng.standard_normal(field.shape)) / math.sqrt(2)
+    import torch
+    plan = make_plan(case, taps)
+    ws = plan.new_workspace(case.L, case.batch)
+    y = plan.backpropagate_checkpointed(to_storage(field, 0), ws)
+    torch.cuda.synchronize()
+    G = 2.0 * (from_storage(y, 0) - target)
+    gc, gr, gi = plan.grad(to_storage(G, 0), ws, want_ratio=False)
+    torch.cuda.synchronize()
+    assert gr is None
+    o_in, o_taps, _ = oadj.dbp_mode_b_vjp(field[0], oracle_params(case, taps), case.n_fft,
+                                          case.overlap, G[0])
+    assert rel_l2(gc.cpu().numpy(), o_taps, "adjoint/taps-only") <= GTOL
+    assert rel_l2(from_storage(gi, 0)[0], o_in, "adjoint/input-taps-only") <= GTOL
 
 
 def test_adjoint_matches_finite_differences_of_oracle():
@@ -157,4 +179,4 @@ def test_c4_size_gradient_on_sampled_blocks():
         o_taps, o_ratio = o_taps + t, o_ratio + r
     assert rel_l2(gc, o_taps, "c4/taps") <= GTOL
     rel_l2(np.array([gr]), np.array([o_ratio]), "c4/ratio")
-    assert gr == pytest.approx(o_ratio, rel=RATIO_TOL_LONG)
+    assert gr == pytest.approx(o_ratio, rel=GTOL)
