@@ -201,6 +201,34 @@ __device__ __forceinline__ void nlpr_rotation8(const ChainArgs& a, const float* 
     for (int q = 0; q < 8; ++q) dst[q] = rotation_factor(acc[q], rot_tbl);
 }
 
+// x[t] *= h(b_t) for the E slots of thread j of subband group gi, with h read from a half
+// table by |b| (`hh` = one kind of ArgsChain::gvd_half).  Slot t holds lowpass bin
+// kap = j + (NP/E) t, centred bin b = ci + kap (kap < NP/2) or ci + kap - NP.  A subband lies
+// wholly on one side of bin 0 except the centre one (ci = 0, odd subband counts), so each half
+// of the slots reads one contiguous run, ascending or descending, at immediate offsets.
+template <int NP, int E>
+__device__ __forceinline__ void gvd_apply(float2 (&x)[E], const float2* __restrict__ hh, int j,
+                                          int ci) {
+    constexpr int TPF = NP / E;
+    if (ci > 0) {
+        const float2* p0 = hh + (ci + j);
+        const float2* p1 = hh + (ci + j - NP);
+#pragma unroll
+        for (int t = 0; t < E; ++t) x[t] = c_mul(x[t], __ldg((t < E / 2 ? p0 : p1) + TPF * t));
+    } else if (ci < 0) {
+        const float2* p0 = hh + (-ci - j);
+        const float2* p1 = hh + (-ci - j + NP);
+#pragma unroll
+        for (int t = 0; t < E; ++t) x[t] = c_mul(x[t], __ldg((t < E / 2 ? p0 : p1) - TPF * t));
+    } else {
+        const float2* p0 = hh + j;
+        const float2* p1 = hh + (NP - j);
+#pragma unroll
+        for (int t = 0; t < E; ++t)
+            x[t] = c_mul(x[t], __ldg(t < E / 2 ? p0 + TPF * t : p1 - TPF * t));
+    }
+}
+
 // Position of a thread in its CTA: block g of the CTA, polarization p, FFT group gi (subband in
 // the steps, polyphase component at entry/exit) and index j within the group.
 struct ThreadPos {
@@ -360,11 +388,8 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     __syncthreads();
 
     // ---------------- 3. GVD / NLPR steps --------------------------------------------------
-    {
-        const float2* h = a.gvd + (size_t)gi * NP;                  // first GVD (x 1/N)
-#pragma unroll
-        for (int t = 0; t < E; ++t) x[t] = c_mul(x[t], __ldg(h + j + TPF * t));
-    }
+    const int half_len = a.N / 2 + 1;
+    gvd_apply<NP, E>(x, a.gvd_half, j, ci);                        // first GVD (x 1/N)
     save_ckpt(0, x);
     // intensity rows and (cos, sin) rows: see the kLayout* constants
     const bool alias = a.layout == kLayoutAlias;
@@ -440,9 +465,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         }
         if (alias) __syncthreads();
         fft_regs<NP, E, false, true>(x, j, fwd1, fwd2, s_tw, bar, !pp);  // back to subband bins
-        const float2* h = a.gvd + (size_t)((s < a.n_st - 1 ? 1 : 2) * a.n_sb + gi) * NP;
-#pragma unroll
-        for (int t = 0; t < E; ++t) x[t] = c_mul(x[t], __ldg(h + j + TPF * t));
+        gvd_apply<NP, E>(x, a.gvd_half + (s < a.n_st - 1 ? 1 : 2) * half_len, j, ci);
     }
 
     if (a.n_st > 0) save_ckpt(a.n_st + 1, x);

@@ -39,6 +39,7 @@ struct ChainArgs {
     int tbl_bytes;               // shared memory after the G regions: FFT twiddles (+ tap buffers)
     int taps_smem;               // 1: each step's taps are staged in shared memory (4-tap chunks = 3)
     const float2* gvd;           // [3][n_sb][NP]: first (x 1/N), interior (x 1/NP), last (x 1/NP)
+    const float2* gvd_half;      // [3][N/2 + 1]: the same factors by |centred bin|
     const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
     const float2* fft_tw;        // FFT pass twiddles (fft_tw_size(NP))
     const float* taps;           // [n_st][n_sb][n_sb][ntaps_pad]
@@ -66,6 +67,7 @@ struct PlanImpl {
     int tbl_bytes = 0, taps_smem = 0;
     double step_length = 0.0;
     float2* d_gvd = nullptr;      // [3][n_sb][NP]
+    float2* d_gvd_half = nullptr; // [3][N/2 + 1]
     float* d_kdisp = nullptr;     // [n_sb][NP] 2 pi^2 beta2 L_step (f^2 - f_i^2) (ratio derivative)
     float2* d_mix_tw = nullptr;   // [n_sb][N]
     float2* d_fft_tw = nullptr;
