@@ -14,8 +14,10 @@ Modules
 ``adjoint``   FP64 reverse-mode gradient of the chain (taps, splitting ratio, input).
 ``channel``   fine-step split-step Fourier simulation of the Manakov equation (input generator).
 ``evaluate``  matched filter, 1 sample/symbol, mean-phase removal, SNR (Sec. IV-A).
+``coeffs``    analytic CB-ESSFM coefficients: closed-form Volterra kernel and the double
+              integral of its diagonal response (Sec. II-D).
 
 Parity pins live in ``tests/test_oracle_*.py``.  Every function here is pinned by at least one
 check that is not a re-typing of its own formula; see the test module docstrings.
 """
-from . import dbp, channel, evaluate, adjoint  # noqa: F401
+from . import dbp, channel, evaluate, adjoint, coeffs  # noqa: F401
