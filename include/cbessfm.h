@@ -217,6 +217,33 @@ cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int njobs,
                                          cbessfm_stream stream);
 
 /*
+ * cbessfm_analytic_taps -- the CB-ESSFM coefficients of Sec. II-D, for use as plan taps.
+ * For every subband separation d = l - i and tap m in [-N_c, N_c]:
+ *   c_d[m] = (1/R'^2) double integral over mu, nu in [d R' - R'/2, d R' + R'/2] of
+ *            K(mu, nu) exp(j 2 pi (mu - nu) m / R')        (Eq. ESSFM_coefficients_general, P = 1)
+ * with R' = sample_rate / bands and the closed-form Volterra kernel of one step
+ * (Eq. kernel_analytic) built from link->beta2, link->gamma and link->alpha (1/m, power), the
+ * step length L = n_spans * span_length / steps and spans_per_step identical spans per step.
+ * The double integral is a grid x grid midpoint rule, evaluated in FP64 on the current device.
+ *   spans_per_step  1 for a step of one span or less (the step then starts at power
+ *                   step_power[s] and decays over L); k > 1 for steps of k whole spans
+ *                   (steps * k must equal n_spans).
+ *   step_power      host [steps]: the reference power P of each step, in the units in which the
+ *                   field's |u|^2 is given (1 for a field already in sqrt(W) at a span start).
+ *   ntaps           odd, <= 1023; grid in [ntaps, 4096] (quadrature points per axis).
+ *   taps            host out [steps][bands][bands][ntaps]: effective taps
+ *                   w[s][i][l][m + N_c] = step_power[s] Re c_{l-i}[m], times 3/2 for l != i
+ *                   (Eq. NLPR-multiband-2pol); the NLPR is a real phase, so the real part is kept.
+ *   response        host out [2 bands - 1][ntaps][2] (re, im) of c_d[m] for d = -(bands-1) ..
+ *                   bands-1, or NULL.
+ * Synchronous (allocates and frees a small device buffer).  The paper also fits the taps
+ * numerically (Sec. III-B); these analytic ones are the starting point for that.
+ */
+cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int steps,
+                                     int spans_per_step, const double* step_power, int ntaps,
+                                     int grid, double* taps, double* response);
+
+/*
  * cbessfm_get_status -- synchronize `stream`, then read and clear the plan's device status word
  * (bit 0: a bounded wait for a shared-memory copy gave up -> CBESSFM_ERR_TIMEOUT).
  */

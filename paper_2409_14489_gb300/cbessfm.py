@@ -85,6 +85,9 @@ def _load():
     lib.cbessfm_batch_info.restype = c_int
     lib.cbessfm_batch_destroy.argtypes = [P]
     lib.cbessfm_batch_destroy.restype = c_int
+    lib.cbessfm_analytic_taps.argtypes = [ctypes.POINTER(LinkStruct), c_int, c_int, c_int,
+                                          c_void_p, c_int, c_int, c_void_p, c_void_p]
+    lib.cbessfm_analytic_taps.restype = c_int
     return lib
 
 
@@ -110,6 +113,23 @@ def _stream_handle(stream) -> Optional[int]:
 def make_link(beta2: float, span_length: float, n_spans: int, sample_rate: float,
               gamma: float = 0.0, alpha: float = 0.0) -> LinkStruct:
     return LinkStruct(beta2, gamma, alpha, span_length, n_spans, sample_rate)
+
+
+def analytic_taps(link: LinkStruct, bands: int, steps: int, step_power, ntaps: int,
+                  grid: int = 64, spans_per_step: int = 1, with_response: bool = False):
+    """Analytic CB-ESSFM taps ``[steps][bands][bands][ntaps]`` (float64) from
+    ``cbessfm_analytic_taps``; with ``with_response`` also the complex responses c_d[m]
+    ``[2 bands - 1][ntaps]`` for d = l - i = -(bands - 1) .. bands - 1."""
+    pw = np.ascontiguousarray(np.broadcast_to(np.asarray(step_power, dtype=np.float64),
+                                              (steps,)))
+    taps = np.zeros((steps, bands, bands, ntaps), dtype=np.float64)
+    resp = np.zeros((2 * bands - 1, ntaps, 2), dtype=np.float64) if with_response else None
+    _check(_lib.cbessfm_analytic_taps(ctypes.byref(link), bands, steps, spans_per_step,
+                                      pw.ctypes.data, ntaps, grid, taps.ctypes.data,
+                                      resp.ctypes.data if resp is not None else None))
+    if with_response:
+        return taps, resp[..., 0] + 1j * resp[..., 1]
+    return taps
 
 
 class Plan:

@@ -68,3 +68,22 @@ def test_invalid_link_and_null_arguments(lib):
                                          ctypes.byref(h)) == lib.ERR_INVALID_ARG
     assert lib.lib().cbessfm_backpropagate(None, None, None, 10, 1, None) == lib.ERR_INVALID_ARG
     assert lib.lib().cbessfm_plan_destroy(None) == lib.OK
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(bands=0), "bands"), (dict(steps=0), "steps"), (dict(ntaps=4), "ntaps"),
+    (dict(grid=3), "grid"), (dict(spans_per_step=0), "spans_per_step"),
+    (dict(spans_per_step=3), "spans_per_step"), (dict(alpha=-1.0), "alpha"),
+])
+def test_analytic_taps_rejects_invalid_arguments(lib, kw, msg):
+    import numpy as np
+    args = dict(bands=3, steps=2, ntaps=5, grid=16, spans_per_step=1, alpha=4.6e-5)
+    args.update(kw)
+    link = lib.make_link(-21.7e-27, 80e3, 4, 64e9, gamma=1.3e-3, alpha=args["alpha"])
+    taps = np.zeros(4096)
+    pw = np.ones(8)
+    st = lib.lib().cbessfm_analytic_taps(ctypes.byref(link), args["bands"], args["steps"],
+                                         args["spans_per_step"], pw.ctypes.data, args["ntaps"],
+                                         args["grid"], taps.ctypes.data, None)
+    assert st == lib.ERR_INVALID_ARG
+    assert msg in lib.lib().cbessfm_last_error().decode()
