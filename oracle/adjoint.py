@@ -46,6 +46,8 @@ def cbessfm_block_vjp(u: np.ndarray, p: ChainParams, G_out: np.ndarray
 
     Returns (G_in (N, 2) complex, G_taps like p.taps, G_ratio float).
     """
+    if p.per_pol:
+        raise NotImplementedError("the adjoint covers the Manakov NLPR only")
     N = u.shape[0]
     n_sb = p.n_sb
     _, b = subband_bins(N, n_sb)

@@ -39,6 +39,7 @@ class ChainParams:
     n_sb: int               # subbands N_sb
     ratio: float            # splitting ratio rho
     taps: np.ndarray        # (n_st, n_sb, n_sb, ntaps) effective taps, float64
+    per_pol: bool = False   # full-complexity NLPR of Eqs. (NLPR_polx), (NLPR_poly)
 
     @property
     def n_st(self) -> int:
@@ -126,11 +127,44 @@ def nlpr_phase(P: np.ndarray, w: np.ndarray) -> np.ndarray:
     return theta
 
 
-def nlpr(u: np.ndarray, w: np.ndarray) -> np.ndarray:
+def nlpr_phase_per_pol(Px: np.ndarray, Py: np.ndarray, w: np.ndarray):
+    """(theta^x, theta^y) of Eqs. (NLPR_polx), (NLPR_poly), circular in the block.
+
+    theta^x_i[k] = sum_m c_ii[m] (Px_i + Py_i)[k - m] + sum_{l != i} sum_m c_il[m] (2 Px_l + Py_l)[k - m]
+    and theta^y_i with (Px_l + 2 Py_l).  The taps w are the effective ones of the Manakov form
+    (w_ii = c_ii, w_il = (3/2) c_il), so c_il = w_il / 1.5 here; the index is [k - m] as in the
+    Manakov form.  With Px = Py both reduce to Eq. (NLPR-multiband-2pol).
+    """
+    n_sb, n_sub = Px.shape
+    ntaps = w.shape[2]
+    nc = ntaps // 2
+    tx = np.zeros((n_sb, n_sub), dtype=np.float64)
+    ty = np.zeros((n_sb, n_sub), dtype=np.float64)
+    for i in range(n_sb):
+        for l in range(n_sb):
+            for m in range(-nc, nc + 1):
+                px, py = np.roll(Px[l], m), np.roll(Py[l], m)
+                if l == i:
+                    c = w[i, l, m + nc]
+                    tx[i] += c * (px + py)
+                    ty[i] += c * (px + py)
+                else:
+                    c = w[i, l, m + nc] / 1.5
+                    tx[i] += c * (2.0 * px + py)
+                    ty[i] += c * (px + 2.0 * py)
+    return tx, ty
+
+
+def nlpr(u: np.ndarray, w: np.ndarray, per_pol: bool = False) -> np.ndarray:
     """Nonlinear phase rotation of all subbands (Fig. 3): intensity, MIMO FIR, rotation.
 
-    u: (n_sb, N', 2) subband time samples (x, y); returns u * exp(+j theta_i) on both pols.
+    u: (n_sb, N', 2) subband time samples (x, y); returns u * exp(+j theta_i) on both pols, or
+    x * exp(+j theta^x_i), y * exp(+j theta^y_i) with ``per_pol``.
     """
+    if per_pol:
+        Px, Py = np.abs(u[..., 0]) ** 2, np.abs(u[..., 1]) ** 2
+        tx, ty = nlpr_phase_per_pol(Px, Py, w)
+        return np.stack([u[..., 0] * np.exp(1j * tx), u[..., 1] * np.exp(1j * ty)], axis=-1)
     P = np.abs(u[..., 0]) ** 2 + np.abs(u[..., 1]) ** 2
     theta = nlpr_phase(P, w)
     return u * np.exp(1j * theta)[..., None]
@@ -158,7 +192,7 @@ def cbessfm_block(u: np.ndarray, p: ChainParams, trace: Optional[List] = None) -
             us = subband_to_time(X, N)
             if trace is not None:
                 trace.append(("pre_nlpr", us.copy()))
-            us = nlpr(us, p.taps[s])
+            us = nlpr(us, p.taps[s], p.per_pol)
             if trace is not None:
                 trace.append(("post_nlpr", us.copy()))
             X = time_to_subband(us, N)
