@@ -412,6 +412,16 @@ def run_gpu(args, wl, taps):
             forms["adjoint"] = form_adjoint(max(3, min(args.steps, 10)), 2)
         except Exception as exc:
             forms["adjoint"] = {"error": repr(exc)}
+        try:
+            # the same c2 launch with the full-complexity per-polarization NLPR (Eqs. NLPR_polx/poly)
+            plan.set_nlpr_mode(True)
+            t_pp = _events_ms(lambda: plan.backpropagate(x, y), max(3, min(args.steps, 10)), 2)
+            plan.set_nlpr_mode(False)
+            forms["per_polarization_nlpr"] = {
+                "workload": "c2_wdm15 as above, per-polarization NLPR", "ms_per_step": t_pp,
+                "value": sym_per_step / (t_pp / 1e3), "unit": UNIT, "gpu_launches_per_step": 1}
+        except Exception as exc:
+            forms["per_polarization_nlpr"] = {"error": repr(exc)}
         cpu_val, cpu_desc = cpu_baseline(wl, taps, fields)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

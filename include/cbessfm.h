@@ -244,6 +244,20 @@ cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int st
                                      int grid, double* taps, double* response);
 
 /*
+ * cbessfm_set_nlpr_mode -- 0 (default): the NLPR of Eq. (NLPR-multiband-2pol), one phase for
+ * both polarizations of a subband (intensity |x|^2 + |y|^2, XPM weighted by the effective taps).
+ * 1: the full-complexity form of Eqs. (NLPR_polx), (NLPR_poly), a phase per polarization with
+ * co-polarized XPM twice as effective as cross-polarized XPM.  The taps keep their meaning
+ * (w_il = (3/2) c_il for l != i), so with equal intensities in x and y both forms agree; the
+ * FIR index is [k - m] in both.  The per-polarization form needs shared memory for a second set
+ * of intensity rows: CBESSFM_ERR_UNSUPPORTED (plan unchanged) if they do not fit, and for
+ * FP16/BF16 storage.  Gradients (cbessfm_grad) and cbessfm_batch_run_noalloc support mode 0
+ * only; cbessfm_batch_* runs both.  Synchronous with respect to the host, not to the
+ * device: do not call while launches of the plan are in flight.
+ */
+cbessfm_status cbessfm_set_nlpr_mode(cbessfm_plan* plan, int per_polarization);
+
+/*
  * cbessfm_get_status -- synchronize `stream`, then read and clear the plan's device status word
  * (bit 0: a bounded wait for a shared-memory copy gave up -> CBESSFM_ERR_TIMEOUT).
  */

@@ -85,6 +85,8 @@ def _load():
     lib.cbessfm_batch_info.restype = c_int
     lib.cbessfm_batch_destroy.argtypes = [P]
     lib.cbessfm_batch_destroy.restype = c_int
+    lib.cbessfm_set_nlpr_mode.argtypes = [P, c_int]
+    lib.cbessfm_set_nlpr_mode.restype = c_int
     lib.cbessfm_analytic_taps.argtypes = [ctypes.POINTER(LinkStruct), c_int, c_int, c_int,
                                           c_void_p, c_int, c_int, c_void_p, c_void_p]
     lib.cbessfm_analytic_taps.restype = c_int
@@ -265,6 +267,11 @@ class Plan:
         c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float32))
         _check(_lib.cbessfm_set_coeffs(self._h, c.ctypes.data, 0, _stream_handle(stream)))
         return c
+
+    def set_nlpr_mode(self, per_polarization: bool):
+        """Switch between the Manakov NLPR (False) and the per-polarization NLPR (True)."""
+        _check(_lib.cbessfm_set_nlpr_mode(self._h, 1 if per_polarization else 0))
+        self.per_polarization = bool(per_polarization)
 
     def set_ratio(self, ratio: float, stream=None):
         _check(_lib.cbessfm_set_ratio(self._h, float(ratio), _stream_handle(stream)))

@@ -569,6 +569,8 @@ cbessfm_status check_common(const cbessfm_plan* plan, int64_t n_samples, int bat
     if (p == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     if (p->storage != CBESSFM_C64)
         return fail(CBESSFM_ERR_UNSUPPORTED, "gradients need complex64 storage");
+    if (p->per_pol)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "gradients cover the Manakov NLPR only");
     if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
     if (workspace == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(workspace) & 255u)

@@ -116,11 +116,20 @@ bool choose_layout(PlanImpl& p, int tb, int tpf) {
         int layout, region, nlpr_off, exb_off, pbuf;
     };
     std::vector<Cand> cands;
-    // ping-pong exchange arrays with two intensity buffers, then with one
-    cands.push_back({kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, prow});
-    cands.push_back({kLayoutPingPong, 2 * exch + prow, 2 * exch, exch, 0});
-    cands.push_back({kLayoutSeparate, exch + prow + csr, exch, 0, 0});
-    cands.push_back({kLayoutAlias, round_up(std::max(exch, prow + csr), 128), 0, 0, 0});
+    if (p.per_pol) {
+        // the Px - Py rows take the second intensity buffer (one intensity buffer, so the
+        // barrier after the FIR spans the CTA)
+        cands.push_back({kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, 0});
+        cands.push_back({kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, 0});
+        cands.push_back({kLayoutSeparate, exch + 2 * prow + csr, exch, 0, 0});
+        cands.push_back({kLayoutAlias, round_up(std::max(exch, 2 * prow + csr), 128), 0, 0, 0});
+    } else {
+        // ping-pong exchange arrays with two intensity buffers, then with one
+        cands.push_back({kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, prow});
+        cands.push_back({kLayoutPingPong, 2 * exch + prow, 2 * exch, exch, 0});
+        cands.push_back({kLayoutSeparate, exch + prow + csr, exch, 0, 0});
+        cands.push_back({kLayoutAlias, round_up(std::max(exch, prow + csr), 128), 0, 0, 0});
+    }
     // Optional override of the automatic choice (tuning): CBESSFM_SMEM_LAYOUT = pingpong2 |
     // pingpong1 | separate | alias.  A layout that does not fit falls back to the automatic one.
     int forced = -1;
@@ -192,6 +201,7 @@ ChainArgs make_chain_args(const PlanImpl& p) {
     a.pbuf_bytes = p.pbuf_bytes;
     a.tbl_bytes = p.tbl_bytes;
     a.taps_smem = p.taps_smem;
+    a.per_pol = p.per_pol;
     a.gvd = p.d_gvd;
     a.gvd_half = p.d_gvd_half;
     a.mix_tw = p.d_mix_tw;
@@ -413,6 +423,27 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
     a.n_blocks = (int)n_blocks;
     const cudaError_t e = launch_forward(p, a, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_set_nlpr_mode(cbessfm_plan* plan, int per_polarization) {
+    clear_error();
+    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    if (per_polarization != 0 && per_polarization != 1)
+        return fail(CBESSFM_ERR_INVALID_ARG, "per_polarization must be 0 or 1");
+    PlanImpl& p = plan->impl;
+    if (per_polarization && p.storage != CBESSFM_C64)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "the per-polarization NLPR needs complex64 storage");
+    if (p.per_pol == per_polarization) return CBESSFM_OK;
+    PlanImpl trial = p;
+    trial.per_pol = per_polarization;
+    const int tpf = p.n_fft / fft_slots(p.n_fft);
+    const int tb = 2 * p.n_sb * tpf;
+    if (!choose_layout(trial, tb, tpf))
+        return fail(CBESSFM_ERR_UNSUPPORTED,
+                    "the per-polarization NLPR of %d bands at n_fft %d does not fit shared memory",
+                    p.n_sb, p.n_fft);
+    p = trial;
     return CBESSFM_OK;
 }
 

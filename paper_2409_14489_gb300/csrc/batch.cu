@@ -21,7 +21,7 @@
 struct cbessfm_batch {
     struct Group {
         int np = 0, n_sb = 0, storage = 0;
-        int G = 1, threads = 0, region_bytes = 0, tbl_bytes = 0, grid = 0;
+        int G = 1, threads = 0, region_bytes = 0, tbl_bytes = 0, per_pol = 0, grid = 0;
         int item_off = 0, n_items = 0;
     };
     std::vector<Group> groups;
@@ -57,7 +57,7 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
     if (jobs == nullptr || njobs < 1) return fail(CBESSFM_ERR_INVALID_ARG, "no jobs");
 
     std::vector<ChainArgs> args(njobs);
-    std::map<std::tuple<int, int, int>, std::vector<int>> by_shape;
+    std::map<std::tuple<int, int, int, int>, std::vector<int>> by_shape;
     for (int k = 0; k < njobs; ++k) {
         const cbessfm_job& jb = jobs[k];
         const PlanImpl* p = plan_impl(jb.plan);
@@ -80,7 +80,7 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
         a.batch = 1;
         a.n_blocks = (int)nb;
         args[k] = a;
-        by_shape[std::make_tuple(p->n_fft, p->n_sb, (int)p->storage)].push_back(k);
+        by_shape[std::make_tuple(p->n_fft, p->n_sb, (int)p->storage, p->per_pol)].push_back(k);
     }
 
     cbessfm_batch* b = new (std::nothrow) cbessfm_batch;
@@ -101,6 +101,7 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
         gr.np = std::get<0>(kv.first);
         gr.n_sb = std::get<1>(kv.first);
         gr.storage = std::get<2>(kv.first);
+        gr.per_pol = std::get<3>(kv.first);
         const int tpf = gr.np / fft_slots(gr.np);
         const int tb = 2 * gr.n_sb * tpf;
         bool any_taps = false;
@@ -175,7 +176,8 @@ cbessfm_status cbessfm_batch_run(const cbessfm_batch* b, cbessfm_stream stream) 
         if (e == cudaSuccess)
             e = launch_forward_persistent(gr.np, gr.storage, b->d_jobs, b->d_items + gr.item_off,
                                           gr.n_items, b->d_counters + gi, gr.n_sb, gr.G,
-                                          gr.region_bytes, gr.tbl_bytes, gr.threads, gr.grid, st);
+                                          gr.region_bytes, gr.tbl_bytes, gr.per_pol, gr.threads,
+                                          gr.grid, st);
         if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     }
     return CBESSFM_OK;

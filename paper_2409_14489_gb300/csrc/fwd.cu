@@ -118,11 +118,12 @@ static cudaError_t launch_st(int np, const ChainArgs& a, int threads, cudaStream
 template <int ST>
 static cudaError_t persistent_st(int np, const ChainArgs* jobs, const int2* items, int n_items,
                                  unsigned int* counter, int n_sb, int G, int region_bytes,
-                                 int tbl_bytes, int threads, int grid, cudaStream_t stream) {
+                                 int tbl_bytes, int per_pol, int threads, int grid,
+                                 cudaStream_t stream) {
 #define CB_CASE(NP)                                                                              \
     case NP:                                                                                     \
         return fwd_persistent_launch<NP, ST>(jobs, items, n_items, counter, n_sb, G, region_bytes, \
-                                             tbl_bytes, threads, grid, stream);
+                                             tbl_bytes, per_pol, threads, grid, stream);
     switch (np) {
         CB_CASE(16) CB_CASE(32) CB_CASE(64) CB_CASE(128) CB_CASE(256) CB_CASE(512) CB_CASE(1024)
         CB_CASE(2048)
@@ -145,12 +146,12 @@ static cudaError_t occupancy_st(int np, int threads, int smem_bytes, int* ctas) 
 
 cudaError_t launch_forward_persistent(int np, int storage, const ChainArgs* jobs, const int2* items,
                                       int n_items, unsigned int* counter, int n_sb, int G,
-                                      int region_bytes, int tbl_bytes, int threads, int grid,
-                                      cudaStream_t stream) {
+                                      int region_bytes, int tbl_bytes, int per_pol, int threads,
+                                      int grid, cudaStream_t stream) {
     switch (storage) {
-        case 0: return persistent_st<0>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, tbl_bytes, threads, grid, stream);
-        case 1: return persistent_st<1>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, tbl_bytes, threads, grid, stream);
-        case 2: return persistent_st<2>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, tbl_bytes, threads, grid, stream);
+        case 0: return persistent_st<0>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, tbl_bytes, per_pol, threads, grid, stream);
+        case 1: return persistent_st<1>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, tbl_bytes, per_pol, threads, grid, stream);
+        case 2: return persistent_st<2>(np, jobs, items, n_items, counter, n_sb, G, region_bytes, tbl_bytes, per_pol, threads, grid, stream);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -11,11 +11,11 @@ namespace cbessfm {
     template cudaError_t fwd_prepare<NP, 1>(int);                                       \
     template cudaError_t fwd_prepare<NP, 2>(int);                                       \
     template cudaError_t fwd_persistent_launch<NP, 0>(const ChainArgs*, const int2*, int,  \
-        unsigned int*, int, int, int, int, int, int, cudaStream_t);                          \
+        unsigned int*, int, int, int, int, int, int, int, cudaStream_t);                          \
     template cudaError_t fwd_persistent_launch<NP, 1>(const ChainArgs*, const int2*, int,  \
-        unsigned int*, int, int, int, int, int, int, cudaStream_t);                          \
+        unsigned int*, int, int, int, int, int, int, int, cudaStream_t);                          \
     template cudaError_t fwd_persistent_launch<NP, 2>(const ChainArgs*, const int2*, int,  \
-        unsigned int*, int, int, int, int, int, int, cudaStream_t);                          \
+        unsigned int*, int, int, int, int, int, int, int, cudaStream_t);                          \
     template cudaError_t fwd_persistent_occupancy<NP, 0>(int, int, int*);               \
     template cudaError_t fwd_persistent_occupancy<NP, 1>(int, int, int*);               \
     template cudaError_t fwd_persistent_occupancy<NP, 2>(int, int, int*);

@@ -119,11 +119,13 @@ __device__ __forceinline__ int cpad(int k) { return k + (k >> 4); }
 // WS: the taps `wbase` are in shared memory (plain loads) instead of global memory.
 template <int E, int NCH, bool WS = false>
 __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restrict__ wbase,
-                                     const float* __restrict__ rows0, int k0, float (&acc)[8]) {
+                                     const float* __restrict__ rows0, int k0, float (&acc)[8],
+                                     int skip_l = -1) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.f;
     const int m0 = a.H + a.p_off + k0 + a.nc - 3;      // row index of chunk 0's window
     for (int l = 0; l < a.n_sb; ++l) {
+        if (l == skip_l) continue;                     // uniform across the subband group
         const float* pl = rows0 + l * a.pstride;
         if constexpr (NCH > 0) {
             const float4* wrow = wbase + l * NCH;
@@ -179,26 +181,47 @@ __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restric
 // theta_i[k] = sum_l sum_m w[s][i][l][m + nc] P_l[k - m]; stores (cos theta, sin theta).
 // `s_taps` is the step's tap buffer in shared memory when a.taps_smem is set.
 template <int E>
+__device__ __forceinline__ void fir8_any(const ChainArgs& a, const float* __restrict__ rows0,
+                                         const float4* __restrict__ s_taps, int s, int i, int k0,
+                                         float (&acc)[8], int skip_l) {
+    if (a.taps_smem) {
+        fir8<E, 3, true>(a, s_taps + i * a.n_sb * 3, rows0, k0, acc, skip_l);   // 9 to 12 taps
+    } else {
+        const float4* wbase = reinterpret_cast<const float4*>(
+            a.taps + (size_t)(s * a.n_sb + i) * a.n_sb * a.ntaps_pad);
+        if (a.nchunks == 3) {
+            fir8<E, 3>(a, wbase, rows0, k0, acc, skip_l);
+        } else {
+            fir8<E, 0>(a, wbase, rows0, k0, acc, skip_l);
+        }
+    }
+}
+
+// Manakov form: the rotation factors of 8 samples.  Per-polarization form (PERPOL): the
+// two angles theta^x = theta + delta and theta^y = theta - delta, where theta is the Manakov
+// phase and delta = (1/3) sum_{l != i} w_il (Px_l - Py_l) (the D rows follow the P rows): with
+// w_il = (3/2) c_il, Eqs. (NLPR_polx/poly) weigh XPM by (2 Px + Py) / 1.5 and (Px + 2 Py) / 1.5.
+template <int E, bool PERPOL>
 __device__ __forceinline__ void nlpr_rotation8(const ChainArgs& a, const float* __restrict__ prow0,
                                                float2* __restrict__ cs_row,
                                                const float2* __restrict__ rot_tbl,
                                                const float4* __restrict__ s_taps, int s, int i,
                                                int k0) {
     float acc[8];
-    if (a.taps_smem) {
-        fir8<E, 3, true>(a, s_taps + i * a.n_sb * 3, prow0, k0, acc);     // 9 to 12 taps
-    } else {
-        const float4* wbase = reinterpret_cast<const float4*>(
-            a.taps + (size_t)(s * a.n_sb + i) * a.n_sb * a.ntaps_pad);
-        if (a.nchunks == 3) {
-            fir8<E, 3>(a, wbase, prow0, k0, acc);
-        } else {
-            fir8<E, 0>(a, wbase, prow0, k0, acc);
-        }
-    }
+    fir8_any<E>(a, prow0, s_taps, s, i, k0, acc, -1);
     float2* dst = cs_row + cpad(k0);                   // k0 % 16 in {0, 8}: no carry below
+    if constexpr (PERPOL) {
+        float dl[8];
+        fir8_any<E>(a, prow0 + a.n_sb * a.pstride, s_taps, s, i, k0, dl, i);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) dst[q] = rotation_factor(acc[q], rot_tbl);
+        for (int q = 0; q < 8; ++q) {
+            const float d = dl[q] * (1.0f / 3.0f);
+            dst[q] = make_float2(acc[q] + d, acc[q] - d);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = rotation_factor(acc[q], rot_tbl);
+    }
 }
 
 // x[t] *= h(b_t) for the E slots of thread j of subband group gi, with h read from a half
@@ -255,7 +278,7 @@ __device__ __forceinline__ ThreadPos thread_pos(int n_sb) {
 // CTA call it together (it contains block-wide barriers); `real` = false runs a zero block and
 // stores nothing.  `bar_g` is the slot's mbarrier, used with phase `parity`.  Returns false if a
 // bounded wait for the staging copy gave up (the caller must then stop).
-template <int NP, int ST, bool CKPT = false>
+template <int NP, int ST, bool CKPT = false, bool PERPOL = false>
 __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* smem,
                                             int region_bytes, uint64_t* bar_g, uint32_t parity,
                                             const float2* __restrict__ s_rot,
@@ -394,8 +417,9 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     // intensity rows and (cos, sin) rows: see the kLayout* constants
     const bool alias = a.layout == kLayoutAlias;
     float* const prowA = reinterpret_cast<float*>(region + a.nlpr_off);
-    float2* const cs_row = pp ? (NPASS > 2 ? grpB : grpA)
-                              : reinterpret_cast<float2*>(prowA + a.n_sb * a.pstride) + gi * CSL;
+    float2* const cs_row =
+        pp ? (NPASS > 2 ? grpB : grpA)
+           : reinterpret_cast<float2*>(prowA + (PERPOL ? 2 : 1) * a.n_sb * a.pstride) + gi * CSL;
     const bool group_cs_bar = pp && a.pbuf_bytes > 0;
     const int cs_base = (TPF >= 16) ? cpad(j) : 0;
     const int n4 = a.n_sb * a.n_sb * 3;               // float4 per step's taps (12 per row)
@@ -424,21 +448,36 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
             constexpr bool kFlat = (E == 16) && (TPF % 64 == 0);
             const bool flat = kFlat && a.H <= TPF;
             float* pbase = prow + pswz<E>(mb + j);
+            const int dstride = PERPOL ? a.n_sb * a.pstride : 0;     // D rows follow P rows
 #pragma unroll
             for (int t = 0; t < E; ++t) {
-                float pw = fmaf(x[t].x, x[t].x, x[t].y * x[t].y);
-                pw += __shfl_xor_sync(0xffffffffu, pw, 1);          // |x|^2 + |y|^2
+                const float own = fmaf(x[t].x, x[t].x, x[t].y * x[t].y);
+                const float oth = __shfl_xor_sync(0xffffffffu, own, 1);
+                const float pw = own + oth;                          // |x|^2 + |y|^2
                 if (p == 0) {
                     const int n = j + TPF * t;
+                    const float dv = own - oth;                      // |x|^2 - |y|^2
                     if (flat) {
                         pbase[TPF * t] = pw;
-                        if (t == 0 && n < a.H) prow[pswz<E>(mb + n + NP)] = pw;
-                        if (t == E - 1 && n >= NP - a.H) prow[pswz<E>(mb + n - NP)] = pw;
+                        if constexpr (PERPOL) pbase[TPF * t + dstride] = dv;
+                        if (t == 0 && n < a.H) {
+                            prow[pswz<E>(mb + n + NP)] = pw;
+                            if constexpr (PERPOL) prow[pswz<E>(mb + n + NP) + dstride] = dv;
+                        }
+                        if (t == E - 1 && n >= NP - a.H) {
+                            prow[pswz<E>(mb + n - NP)] = pw;
+                            if constexpr (PERPOL) prow[pswz<E>(mb + n - NP) + dstride] = dv;
+                        }
                     } else {
                         prow[pswz<E>(mb + n)] = pw;
                         // circular halo: H <= NP (ntaps <= NP/2), so one copy per side suffices
                         if (n < a.H) prow[pswz<E>(mb + n + NP)] = pw;
                         if (n >= NP - a.H) prow[pswz<E>(mb + n - NP)] = pw;
+                        if constexpr (PERPOL) {
+                            prow[pswz<E>(mb + n) + dstride] = dv;
+                            if (n < a.H) prow[pswz<E>(mb + n + NP) + dstride] = dv;
+                            if (n >= NP - a.H) prow[pswz<E>(mb + n - NP) + dstride] = dv;
+                        }
                     }
                 }
             }
@@ -447,7 +486,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         __syncthreads();
 #pragma unroll
         for (int h8 = 0; h8 < E / 16; ++h8)
-            nlpr_rotation8<E>(a, prow0, cs_row, s_rot, taps_buf, s, gi,
+            nlpr_rotation8<E, PERPOL>(a, prow0, cs_row, s_rot, taps_buf, s, gi,
                               E * j + (E / 2) * p + 8 * h8);
         // (cos, sin) of subband gi are written and read by group gi only.  With two intensity
         // buffers nothing else is shared before the next step's intensity barrier: a group that
@@ -459,8 +498,11 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         }
 #pragma unroll
         for (int t = 0; t < E; ++t) {
-            const float2 rot = (TPF >= 16) ? cs_row[cs_base + (TPF + TPF / 16) * t]
-                                           : cs_row[cpad(j + TPF * t)];
+            const float2 r = (TPF >= 16) ? cs_row[cs_base + (TPF + TPF / 16) * t]
+                                         : cs_row[cpad(j + TPF * t)];
+            // per-polarization form: r holds the two angles
+            float2 rot = r;
+            if constexpr (PERPOL) rot = rotation_factor(p == 0 ? r.x : r.y, s_rot);
             x[t] = c_mul(x[t], rot);
         }
         if (alias) __syncthreads();
@@ -514,7 +556,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 
 // One launch over `a.batch` sequences of one plan: CTA b runs blocks b G .. b G + G - 1 of the
 // flattened (sequence, block) list.
-template <int NP, int ST>
+template <int NP, int ST, bool PERPOL = false>
 __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kMaxG];
@@ -533,8 +575,8 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
     const bool real = item < total;
     const int seq = real ? (int)(item / a.n_blocks) : 0;
     const int blk = real ? (int)(item % a.n_blocks) : 0;
-    chain_block<NP, ST>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, s_tw, s_taps, tp, real,
-                        seq, blk);
+    chain_block<NP, ST, false, PERPOL>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, s_tw,
+                                       s_taps, tp, real, seq, blk);
 }
 
 // Forward launch that also writes the adjoint's checkpoints (complex64 storage).
@@ -565,7 +607,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_ckpt_kernel(const ChainArg
 // CTAs claim work items (job, first block) from `counter` in the order of `items` (sorted by
 // decreasing cost on the host) until the list is exhausted.  Each item runs G consecutive blocks
 // of one job; per-job parameters come from `jobs`.
-template <int NP, int ST>
+template <int NP, int ST, bool PERPOL = false>
 __global__ void __launch_bounds__(640, 1) cbessfm_fwd_persistent_kernel(
     const ChainArgs* __restrict__ jobs, const int2* __restrict__ items, int n_items,
     unsigned int* __restrict__ counter, int n_sb, int G, int region_bytes) {
@@ -601,8 +643,9 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_persistent_kernel(
         }
         const int blk = w.y + tp.g;
         const bool real = blk < s_job.n_blocks;
-        if (!chain_block<NP, ST>(s_job, smem, region_bytes, &bars[tp.g], it & 1u, s_rot, s_tw,
-                                 s_taps, tp, real, 0, real ? blk : 0))
+        if (!chain_block<NP, ST, false, PERPOL>(s_job, smem, region_bytes, &bars[tp.g], it & 1u,
+                                                s_rot, s_tw, s_taps, tp, real, 0,
+                                                real ? blk : 0))
             return;
         __syncthreads();                               // s_item / s_job reuse
     }
@@ -615,6 +658,12 @@ cudaError_t fwd_launch(const ChainArgs& a, int threads, cudaStream_t stream) {
     const long long grid = (total + a.G - 1) / a.G;
     if (grid <= 0) return cudaSuccess;
     const size_t smem = (size_t)a.G * a.region_bytes + a.tbl_bytes;
+    if constexpr (ST == 0) {
+        if (a.per_pol) {
+            cbessfm_fwd_kernel<NP, 0, true><<<(unsigned)grid, threads, smem, stream>>>(a);
+            return cudaGetLastError();
+        }
+    }
     cbessfm_fwd_kernel<NP, ST><<<(unsigned)grid, threads, smem, stream>>>(a);
     return cudaGetLastError();
 }
@@ -624,16 +673,33 @@ cudaError_t fwd_prepare(int smem_bytes) {
     cudaError_t e = cudaFuncSetAttribute(cbessfm_fwd_kernel<NP, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(cbessfm_fwd_persistent_kernel<NP, ST>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    e = cudaFuncSetAttribute(cbessfm_fwd_persistent_kernel<NP, ST>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if constexpr (ST == 0) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(cbessfm_fwd_kernel<NP, 0, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(cbessfm_fwd_persistent_kernel<NP, 0, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    }
+    return e;
 }
 
 template <int NP, int ST>
 cudaError_t fwd_persistent_launch(const ChainArgs* jobs, const int2* items, int n_items,
                                   unsigned int* counter, int n_sb, int G, int region_bytes,
-                                  int tbl_bytes, int threads, int grid, cudaStream_t stream) {
+                                  int tbl_bytes, int per_pol, int threads, int grid,
+                                  cudaStream_t stream) {
     if (n_items <= 0 || grid <= 0) return cudaSuccess;
     const size_t smem = (size_t)G * region_bytes + tbl_bytes;
+    if constexpr (ST == 0) {
+        if (per_pol) {
+            cbessfm_fwd_persistent_kernel<NP, 0, true><<<grid, threads, smem, stream>>>(
+                jobs, items, n_items, counter, n_sb, G, region_bytes);
+            return cudaGetLastError();
+        }
+    }
     cbessfm_fwd_persistent_kernel<NP, ST><<<grid, threads, smem, stream>>>(
         jobs, items, n_items, counter, n_sb, G, region_bytes);
     return cudaGetLastError();

@@ -13,7 +13,8 @@ cudaError_t fwd_prepare(int smem_bytes);
 template <int NP, int ST>
 cudaError_t fwd_persistent_launch(const ChainArgs* jobs, const int2* items, int n_items,
                                   unsigned int* counter, int n_sb, int G, int region_bytes,
-                                  int tbl_bytes, int threads, int grid, cudaStream_t stream);
+                                  int tbl_bytes, int per_pol, int threads, int grid,
+                                  cudaStream_t stream);
 template <int NP, int ST>
 cudaError_t fwd_persistent_occupancy(int threads, int smem_bytes, int* ctas_per_sm);
 
@@ -25,11 +26,11 @@ cudaError_t fwd_persistent_occupancy(int threads, int smem_bytes, int* ctas_per_
     extern template cudaError_t fwd_prepare<NP, 1>(int);                                  \
     extern template cudaError_t fwd_prepare<NP, 2>(int);                                  \
     extern template cudaError_t fwd_persistent_launch<NP, 0>(const ChainArgs*, const int2*, int, \
-        unsigned int*, int, int, int, int, int, int, cudaStream_t);                            \
+        unsigned int*, int, int, int, int, int, int, int, cudaStream_t);                            \
     extern template cudaError_t fwd_persistent_launch<NP, 1>(const ChainArgs*, const int2*, int, \
-        unsigned int*, int, int, int, int, int, int, cudaStream_t);                            \
+        unsigned int*, int, int, int, int, int, int, int, cudaStream_t);                            \
     extern template cudaError_t fwd_persistent_launch<NP, 2>(const ChainArgs*, const int2*, int, \
-        unsigned int*, int, int, int, int, int, int, cudaStream_t);                            \
+        unsigned int*, int, int, int, int, int, int, int, cudaStream_t);                            \
     extern template cudaError_t fwd_persistent_occupancy<NP, 0>(int, int, int*);          \
     extern template cudaError_t fwd_persistent_occupancy<NP, 1>(int, int, int*);          \
     extern template cudaError_t fwd_persistent_occupancy<NP, 2>(int, int, int*);

@@ -38,6 +38,8 @@ struct ChainArgs {
     int pbuf_bytes;              // bytes from the first to the second intensity-row buffer, or 0
     int tbl_bytes;               // shared memory after the G regions: FFT twiddles (+ tap buffers)
     int taps_smem;               // 1: each step's taps are staged in shared memory (4-tap chunks = 3)
+    int per_pol;                 // 1: per-polarization NLPR of Eqs. (NLPR_polx/poly); the
+                                 //    Px - Py rows follow the intensity rows
     const float2* gvd;           // [3][n_sb][NP]: first (x 1/N), interior (x 1/NP), last (x 1/NP)
     const float2* gvd_half;      // [3][N/2 + 1]: the same factors by |centred bin|
     const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
@@ -64,7 +66,7 @@ struct PlanImpl {
     int N = 16, n_ov = 0, V = 16;
     int nc = 0, ntaps_pad = 4, nchunks = 1, H = 4, p_off = 3, pstride = 32;
     int region_bytes = 0, nlpr_off = 0, layout = 0, exb_off = 0, pbuf_bytes = 0, G = 1, threads = 0;
-    int tbl_bytes = 0, taps_smem = 0;
+    int tbl_bytes = 0, taps_smem = 0, per_pol = 0;
     double step_length = 0.0;
     float2* d_gvd = nullptr;      // [3][n_sb][NP]
     float2* d_gvd_half = nullptr; // [3][N/2 + 1]
@@ -118,8 +120,8 @@ const PlanImpl* plan_impl(const cbessfm_plan* plan);
 // Persistent batched launch of the forward kernel for one (NP, storage) group.
 cudaError_t launch_forward_persistent(int np, int storage, const ChainArgs* jobs, const int2* items,
                                       int n_items, unsigned int* counter, int n_sb, int G,
-                                      int region_bytes, int tbl_bytes, int threads, int grid,
-                                      cudaStream_t stream);
+                                      int region_bytes, int tbl_bytes, int per_pol, int threads,
+                                      int grid, cudaStream_t stream);
 cudaError_t forward_persistent_occupancy(int np, int storage, int threads, int smem_bytes,
                                          int* ctas_per_sm);
 

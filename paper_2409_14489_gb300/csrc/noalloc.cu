@@ -197,6 +197,8 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
         } else if (p->n_fft != np || p->n_sb != n_sb) {
             return fail(CBESSFM_ERR_UNSUPPORTED, "job %d: all jobs must share n_fft and bands", k);
         }
+        if (p->per_pol)
+            return fail(CBESSFM_ERR_UNSUPPORTED, "job %d: the per-polarization NLPR is not supported here", k);
         const unsigned long long bytes = (unsigned long long)jb.n_samples * 16ull;
         const uintptr_t i0 = reinterpret_cast<uintptr_t>(jb.in), o0 = reinterpret_cast<uintptr_t>(jb.out);
         if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "job %d: out overlaps in", k);
