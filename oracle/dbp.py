@@ -247,3 +247,49 @@ def dbp_mode_b(field: np.ndarray, p: ChainParams, n_fft: int, overlap: int,
         n_keep = min(V, L - b * V)
         out[b * V: b * V + n_keep] = y[n_ov // 2: n_ov // 2 + n_keep]
     return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Mode S: per-step streaming.  The operator sequence of the chain,
+#   G((1 - rho) L) NLPR_0 G(L) NLPR_1 G(L) ... NLPR_{N_st - 1} G(rho L),
+# is cut into one pass per step, pass s = [G_a(s)] NLPR_s G_b(s) with G_a(0) = G((1 - rho) L)
+# (none after), G_b(s) = G(L) and G_b(N_st - 1) = G(rho L).  Every pass runs its own
+# overlap-and-save over the full band (FFT, DEMUX, subband IFFTs, NLPR, FFTs, MUX, IFFT) and the
+# field is stored between passes, so a pass's overlap needs to cover one step's memory only.
+# ---------------------------------------------------------------------------------------------
+
+def _pass_block(u: np.ndarray, p: ChainParams, s: int) -> np.ndarray:
+    """Pass s of mode S on one circular block u (N, 2)."""
+    N = u.shape[0]
+    n_sb = p.n_sb
+    _, b = subband_bins(N, n_sb)
+    freq = b * (p.sample_rate / N)
+    Ls = p.step_length
+    X = demux(np.fft.fft(u, axis=0), n_sb)
+    if s == 0:
+        X = X * gvd_factor(p.beta2, (1.0 - p.ratio) * Ls, freq)[..., None]
+    us = nlpr(subband_to_time(X, N), p.taps[s], p.per_pol)
+    X = time_to_subband(us, N)
+    dz = Ls if s < p.n_st - 1 else p.ratio * Ls
+    X = X * gvd_factor(p.beta2, dz, freq)[..., None]
+    return np.fft.ifft(mux(X), axis=0)
+
+
+def dbp_mode_s(field: np.ndarray, p: ChainParams, n_fft: int, overlap: int) -> np.ndarray:
+    """Mode S: one overlap-and-save pass over the whole sequence per step (N = n_sb n_fft,
+    N_ov = n_sb overlap, the middle V = N - N_ov samples kept).  With N_st = 0 it is mode B."""
+    field = np.asarray(field, dtype=np.complex128)
+    if p.n_st == 0:
+        return dbp_mode_b(field, p, n_fft, overlap)
+    L = field.shape[0]
+    N = p.n_sb * n_fft
+    n_ov = p.n_sb * overlap
+    V, n_blocks = ols_geometry(L, N, n_ov)
+    for s in range(p.n_st):
+        out = np.zeros((L, 2), dtype=np.complex128)
+        for b in range(n_blocks):
+            y = _pass_block(ols_block_input(field, b, N, n_ov), p, s)
+            n_keep = min(V, L - b * V)
+            out[b * V: b * V + n_keep] = y[n_ov // 2: n_ov // 2 + n_keep]
+        field = out
+    return field
