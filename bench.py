@@ -422,6 +422,19 @@ def run_gpu(args, wl, taps):
                 "value": sym_per_step / (t_pp / 1e3), "unit": UNIT, "gpu_launches_per_step": 1}
         except Exception as exc:
             forms["per_polarization_nlpr"] = {"error": repr(exc)}
+        try:
+            # the same c2 workload as one overlap-and-save pass per step (15 launches)
+            ws_s = torch.empty(plan.streamed_workspace_size(sig.n_samples, wl.batch),
+                               dtype=torch.uint8, device="cuda")
+            t_s = _events_ms(lambda: plan.backpropagate_streamed(x, y, ws_s),
+                             max(3, min(args.steps, 10)), 2)
+            forms["streamed"] = {
+                "workload": "c2_wdm15 as above, one overlap-and-save pass per step",
+                "ms_per_step": t_s, "value": sym_per_step / (t_s / 1e3), "unit": UNIT,
+                "gpu_launches_per_step": d.n_st, "workspace_bytes": int(ws_s.numel())}
+            del ws_s
+        except Exception as exc:
+            forms["streamed"] = {"error": repr(exc)}
         cpu_val, cpu_desc = cpu_baseline(wl, taps, fields)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

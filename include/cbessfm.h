@@ -244,6 +244,27 @@ cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int st
                                      int grid, double* taps, double* response);
 
 /*
+ * Streamed form (per-step overlap-and-save).  The chain's operators are regrouped into one
+ * pass per step over the whole sequence: pass s runs [GVD((1 - rho) L_step), for s = 0 only],
+ * the step's NLPR, and GVD(L_step) (GVD(rho L_step) for the last step), each pass with its own
+ * overlap-and-save blocks of the plan's N and N_ov (DEMUX and MUX inside every block, as in
+ * cbessfm_backpropagate), the field going through device memory between passes.  A pass's
+ * overlap must then cover one step's dispersion, not the whole link's; the price is N_st
+ * launches and N_st reads and writes of the field.  The paper runs the whole chain per block;
+ * this form computes the same operator sequence with a different block decomposition, so the
+ * two agree where both overlaps cover their memory.
+ * cbessfm_streamed_workspace_size -- bytes of device workspace for the intermediate fields
+ *   (0, 1 or 2 fields of n_samples * batch complex64 4D samples, each rounded up to 256 bytes).
+ * cbessfm_backpropagate_streamed -- complex64 storage only; in, out and workspace must not
+ *   overlap; asynchronous on `stream`.  With steps <= 1 it is cbessfm_backpropagate.
+ */
+cbessfm_status cbessfm_streamed_workspace_size(const cbessfm_plan* plan, int64_t n_samples,
+                                               int batch, size_t* bytes);
+cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const void* in, void* out,
+                                              void* workspace, size_t ws_bytes, int64_t n_samples,
+                                              int batch, cbessfm_stream stream);
+
+/*
  * cbessfm_set_nlpr_mode -- 0 (default): the NLPR of Eq. (NLPR-multiband-2pol), one phase for
  * both polarizations of a subband (intensity |x|^2 + |y|^2, XPM weighted by the effective taps).
  * 1: the full-complexity form of Eqs. (NLPR_polx), (NLPR_poly), a phase per polarization with

@@ -85,6 +85,12 @@ def _load():
     lib.cbessfm_batch_info.restype = c_int
     lib.cbessfm_batch_destroy.argtypes = [P]
     lib.cbessfm_batch_destroy.restype = c_int
+    lib.cbessfm_streamed_workspace_size.argtypes = [P, c_int64, c_int,
+                                                    ctypes.POINTER(ctypes.c_size_t)]
+    lib.cbessfm_streamed_workspace_size.restype = c_int
+    lib.cbessfm_backpropagate_streamed.argtypes = [P, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
+                                                   c_int64, c_int, c_void_p]
+    lib.cbessfm_backpropagate_streamed.restype = c_int
     lib.cbessfm_set_nlpr_mode.argtypes = [P, c_int]
     lib.cbessfm_set_nlpr_mode.restype = c_int
     lib.cbessfm_analytic_taps.argtypes = [ctypes.POINTER(LinkStruct), c_int, c_int, c_int,
@@ -267,6 +273,26 @@ class Plan:
         c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float32))
         _check(_lib.cbessfm_set_coeffs(self._h, c.ctypes.data, 0, _stream_handle(stream)))
         return c
+
+    def streamed_workspace_size(self, n_samples: int, batch: int = 1) -> int:
+        n = ctypes.c_size_t()
+        _check(_lib.cbessfm_streamed_workspace_size(self._h, n_samples, batch, ctypes.byref(n)))
+        return n.value
+
+    def backpropagate_streamed(self, x, out=None, workspace=None, stream=None):
+        """Per-step streamed form (``cbessfm_backpropagate_streamed``); complex64 only."""
+        import torch
+        batch, L = self._shape(x)
+        if out is None:
+            out = torch.empty_like(x)
+        need = self.streamed_workspace_size(L, batch)
+        if workspace is None and need:
+            workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
+        _check(_lib.cbessfm_backpropagate_streamed(
+            self._h, x.data_ptr(), out.data_ptr(),
+            workspace.data_ptr() if workspace is not None else None,
+            workspace.numel() if workspace is not None else 0, L, batch, _stream_handle(stream)))
+        return out
 
     def set_nlpr_mode(self, per_polarization: bool):
         """Switch between the Manakov NLPR (False) and the per-polarization NLPR (True)."""

@@ -204,6 +204,8 @@ ChainArgs make_chain_args(const PlanImpl& p) {
     a.per_pol = p.per_pol;
     a.gvd = p.d_gvd;
     a.gvd_half = p.d_gvd_half;
+    a.k_first = 0;
+    a.k_last = 2;
     a.mix_tw = p.d_mix_tw;
     a.fft_tw = p.d_fft_tw;
     a.taps = p.d_taps;
@@ -317,7 +319,7 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
         }                                     \
     } while (0)
     CB_TRY(cudaMalloc(&p.d_gvd, sizeof(float2) * 3 * bands * n_fft), "cudaMalloc(gvd)");
-    CB_TRY(cudaMalloc(&p.d_gvd_half, sizeof(float2) * 3 * (p.N / 2 + 1)), "cudaMalloc(gvd half)");
+    CB_TRY(cudaMalloc(&p.d_gvd_half, sizeof(float2) * 4 * (p.N / 2 + 1)), "cudaMalloc(gvd half)");
     CB_TRY(cudaMalloc(&p.d_kdisp, sizeof(float) * bands * n_fft), "cudaMalloc(kdisp)");
     CB_TRY(cudaMalloc(&p.d_mix_tw, sizeof(float2) * mix_tw.size()), "cudaMalloc(mix)");
     CB_TRY(cudaMalloc(&p.d_fft_tw, sizeof(float2) * fft_tw.size()), "cudaMalloc(fft tw)");
@@ -423,6 +425,73 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
     a.n_blocks = (int)n_blocks;
     const cudaError_t e = launch_forward(p, a, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return CBESSFM_OK;
+}
+
+// Streamed form: one launch of the chain per step, each with one NLPR step and its own
+// overlap-and-save; pass s applies the first GVD ((1 - rho) L_step) only when s = 0 and ends
+// with L_step, or rho L_step for the last step.  Intermediate fields alternate between the
+// workspace's two buffers.
+namespace {
+
+size_t streamed_buffers(const PlanImpl& p) { return p.n_st >= 3 ? 2 : (p.n_st == 2 ? 1 : 0); }
+
+}  // namespace
+
+cbessfm_status cbessfm_streamed_workspace_size(const cbessfm_plan* plan, int64_t n_samples,
+                                               int batch, size_t* bytes) {
+    clear_error();
+    if (plan == nullptr || bytes == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan/bytes is NULL");
+    if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
+    const size_t one = ((size_t)n_samples * batch * 16 + 255) / 256 * 256;
+    *bytes = streamed_buffers(plan->impl) * one;
+    return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const void* in, void* out,
+                                              void* workspace, size_t ws_bytes, int64_t n_samples,
+                                              int batch, cbessfm_stream stream) {
+    clear_error();
+    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    const PlanImpl& p = plan->impl;
+    if (p.storage != CBESSFM_C64)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "the streamed form needs complex64 storage");
+    if (p.n_st <= 1) return cbessfm_backpropagate(plan, in, out, n_samples, batch, stream);
+    if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
+    if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
+    const size_t one = ((size_t)n_samples * batch * 16 + 255) / 256 * 256;
+    if (workspace == nullptr || ws_bytes < streamed_buffers(p) * one)
+        return fail(CBESSFM_ERR_INVALID_ARG, "workspace of %zu bytes is smaller than %zu", ws_bytes,
+                    streamed_buffers(p) * one);
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) |
+         reinterpret_cast<uintptr_t>(workspace)) & 15u)
+        return fail(CBESSFM_ERR_INVALID_ARG, "in/out/workspace must be 16-byte aligned");
+    const unsigned long long bytes = (unsigned long long)n_samples * batch * 16ull;
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
+    const uintptr_t w0 = reinterpret_cast<uintptr_t>(workspace), w1 = w0 + streamed_buffers(p) * one;
+    if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
+    if ((i0 < w1 && w0 < i0 + bytes) || (o0 < w1 && w0 < o0 + bytes))
+        return fail(CBESSFM_ERR_ALIAS, "workspace overlaps in or out");
+    const long long n_blocks = (n_samples + p.V - 1) / p.V;
+    if (n_blocks * batch > (1ll << 31) - 1)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
+    unsigned char* buf[2] = {static_cast<unsigned char*>(workspace),
+                             static_cast<unsigned char*>(workspace) + one};
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int s = 0; s < p.n_st; ++s) {
+        ChainArgs a = make_chain_args(p);
+        a.in = s == 0 ? in : buf[(s - 1) & 1];
+        a.out = s == p.n_st - 1 ? out : buf[s & 1];
+        a.L = n_samples;
+        a.batch = batch;
+        a.n_blocks = (int)n_blocks;
+        a.n_st = 1;
+        a.taps = p.d_taps + (size_t)s * p.n_sb * p.n_sb * p.ntaps_pad;
+        a.k_first = s == 0 ? 0 : 3;
+        a.k_last = s == p.n_st - 1 ? 2 : 1;
+        const cudaError_t e = launch_forward(p, a, st);
+        if (e != cudaSuccess) return cuda_fail(e, "streamed pass launch");
+    }
     return CBESSFM_OK;
 }
 

@@ -9,14 +9,19 @@ namespace cbessfm {
 // FP64 table builder: GVD factors of the three step kinds for every subband bin
 // ------------------------------------------------------------------------------------------
 // The forward chain reads the same factors from a half table indexed by |b| (the factor depends
-// on f^2 only): gvd_half[kind][m] = h(m R / N), m = 0 .. N/2, for the three kinds.
+// on f^2 only): gvd_half[kind][m] = h(m R / N), m = 0 .. N/2, for the three kinds, plus a fourth
+// kind, no dispersion with the 1/N scale, that opens the later passes of the streamed form.
 __global__ void build_gvd_half_kernel(float2* __restrict__ half, long long N, double beta2,
                                       double rate, double dz0, double dz1, double dz2,
                                       double scale0, double scale12) {
     const long long per = N / 2 + 1;
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= 3 * per) return;
+    if (idx >= 4 * per) return;
     const int tbl = (int)(idx / per);
+    if (tbl == 3) {
+        half[idx] = make_float2((float)scale0, 0.0f);
+        return;
+    }
     const long long m = idx - tbl * per;
     const double f = (double)m * rate / (double)N;
     const double dz = tbl == 0 ? dz0 : (tbl == 1 ? dz1 : dz2);
@@ -77,7 +82,7 @@ cudaError_t launch_build_gvd(const PlanImpl& p, cudaStream_t stream) {
         1.0 / (double)p.N, 1.0 / (double)np, Ls);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const long long half = 3LL * (p.N / 2 + 1);
+    const long long half = 4LL * (p.N / 2 + 1);
     build_gvd_half_kernel<<<(unsigned)((half + 255) / 256), 256, 0, stream>>>(
         p.d_gvd_half, p.N, p.link.beta2, p.link.sample_rate, dz0, dz1, dz2, 1.0 / (double)p.N,
         1.0 / (double)np);

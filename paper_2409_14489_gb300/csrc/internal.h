@@ -41,7 +41,9 @@ struct ChainArgs {
     int per_pol;                 // 1: per-polarization NLPR of Eqs. (NLPR_polx/poly); the
                                  //    Px - Py rows follow the intensity rows
     const float2* gvd;           // [3][n_sb][NP]: first (x 1/N), interior (x 1/NP), last (x 1/NP)
-    const float2* gvd_half;      // [3][N/2 + 1]: the same factors by |centred bin|
+    const float2* gvd_half;      // [4][N/2 + 1]: the same factors by |centred bin|, and the
+                                 // unit factor (x 1/N) as kind 3
+    int k_first, k_last;         // gvd_half kinds of the first GVD and of the last step's GVD
     const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
     const float2* fft_tw;        // FFT pass twiddles (fft_tw_size(NP))
     const float* taps;           // [n_st][n_sb][n_sb][ntaps_pad]
@@ -69,7 +71,7 @@ struct PlanImpl {
     int tbl_bytes = 0, taps_smem = 0, per_pol = 0;
     double step_length = 0.0;
     float2* d_gvd = nullptr;      // [3][n_sb][NP]
-    float2* d_gvd_half = nullptr; // [3][N/2 + 1]
+    float2* d_gvd_half = nullptr; // [4][N/2 + 1]
     float* d_kdisp = nullptr;     // [n_sb][NP] 2 pi^2 beta2 L_step (f^2 - f_i^2) (ratio derivative)
     float2* d_mix_tw = nullptr;   // [n_sb][N]
     float2* d_fft_tw = nullptr;
