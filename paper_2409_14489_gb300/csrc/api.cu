@@ -204,8 +204,8 @@ ChainArgs make_chain_args(const PlanImpl& p) {
     a.per_pol = p.per_pol;
     a.gvd = p.d_gvd;
     a.gvd_half = p.d_gvd_half;
-    a.k_first = 0;
-    a.k_last = 2;
+    a.gvd_first = p.d_gvd_half;
+    a.gvd_last = p.d_gvd_half + 2 * (p.N / 2 + 1);
     a.mix_tw = p.d_mix_tw;
     a.fft_tw = p.d_fft_tw;
     a.taps = p.d_taps;
@@ -487,8 +487,9 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
         a.n_blocks = (int)n_blocks;
         a.n_st = 1;
         a.taps = p.d_taps + (size_t)s * p.n_sb * p.n_sb * p.ntaps_pad;
-        a.k_first = s == 0 ? 0 : 3;
-        a.k_last = s == p.n_st - 1 ? 2 : 1;
+        const size_t half = (size_t)(p.N / 2 + 1);
+        a.gvd_first = p.d_gvd_half + (s == 0 ? 0 : 3) * half;
+        a.gvd_last = p.d_gvd_half + (s == p.n_st - 1 ? 2 : 1) * half;
         const cudaError_t e = launch_forward(p, a, st);
         if (e != cudaSuccess) return cuda_fail(e, "streamed pass launch");
     }

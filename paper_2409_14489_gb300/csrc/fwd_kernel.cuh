@@ -412,7 +412,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 
     // ---------------- 3. GVD / NLPR steps --------------------------------------------------
     const int half_len = a.N / 2 + 1;
-    gvd_apply<NP, E>(x, a.gvd_half + a.k_first * half_len, j, ci); // first GVD (x 1/N)
+    gvd_apply<NP, E>(x, a.gvd_first, j, ci);                       // first GVD (x 1/N)
     save_ckpt(0, x);
     // intensity rows and (cos, sin) rows: see the kLayout* constants
     const bool alias = a.layout == kLayoutAlias;
@@ -507,7 +507,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         }
         if (alias) __syncthreads();
         fft_regs<NP, E, false, true>(x, j, fwd1, fwd2, s_tw, bar, !pp);  // back to subband bins
-        gvd_apply<NP, E>(x, a.gvd_half + (s < a.n_st - 1 ? 1 : a.k_last) * half_len, j, ci);
+        gvd_apply<NP, E>(x, s < a.n_st - 1 ? a.gvd_half + half_len : a.gvd_last, j, ci);
     }
 
     if (a.n_st > 0) save_ckpt(a.n_st + 1, x);

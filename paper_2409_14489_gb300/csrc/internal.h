@@ -43,7 +43,8 @@ struct ChainArgs {
     const float2* gvd;           // [3][n_sb][NP]: first (x 1/N), interior (x 1/NP), last (x 1/NP)
     const float2* gvd_half;      // [4][N/2 + 1]: the same factors by |centred bin|, and the
                                  // unit factor (x 1/N) as kind 3
-    int k_first, k_last;         // gvd_half kinds of the first GVD and of the last step's GVD
+    const float2* gvd_first;     // gvd_half kind of the first GVD (kind 0, or 3 in later passes)
+    const float2* gvd_last;      // gvd_half kind of the last step's GVD (kind 2, or 1)
     const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
     const float2* fft_tw;        // FFT pass twiddles (fft_tw_size(NP))
     const float* taps;           // [n_st][n_sb][n_sb][ntaps_pad]
