@@ -177,15 +177,15 @@ def _events_ms(fn, steps: int, warmup: int) -> float:
 
 def form_batched(steps: int, warmup: int):
     """Batching form: 256 uneven realizations of the c1 signal model (lengths log-uniform 2^12 ..
-    2^17 symbols, steps in {1,2,4,8,15}, subbands in {1,3,5}, N' and overlap from the measuring
-    autotuner) as one CUDA-graph replay of the persistent per-group launches, next to the same
+    2^17 symbols, steps in {1,2,4,8,15}, subbands in {1,3,5}, N' and overlap from the autotuner's
+    cost model, which is deterministic) as one CUDA-graph replay of the persistent per-group launches, next to the same
     jobs as sequential plain launches."""
     import dataclasses
     import torch
     from paper_2409_14489_gb300 import autotune, cbessfm
     wl = configs.get_workload("c3_batched")
     lk, sig, d = wl.link, wl.signal, wl.dbp
-    tuner = autotune.Autotuner("measure")
+    tuner = autotune.Autotuner("model")
     w0 = lk.gamma * signals.effective_length(lk.alpha, lk.span_length)
     link = cbessfm.make_link(lk.beta2, lk.span_length, lk.n_spans, sig.sample_rate)
     jobs, sym2d = [], 0
