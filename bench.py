@@ -325,7 +325,7 @@ def run_gpu(args, wl, taps):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    from paper_2409_14489_gb300 import cbessfm
+    from paper_2409_14489_gb300 import cbessfm, distributed
     d, lk, sig = wl.dbp, wl.link, wl.signal
     fields = workload_inputs(wl, rank)
     link = cbessfm.make_link(lk.beta2, lk.span_length, lk.n_spans, sig.sample_rate)
@@ -359,11 +359,7 @@ def run_gpu(args, wl, taps):
         dist.barrier()
     clocks = sampler.stop()
     kernel_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = float(sum(kernel_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = distributed.max_over_ranks(float(sum(kernel_ms)))
     if plan.status() != 0:
         raise RuntimeError("device status reported an error during the timed launches")
 
@@ -387,11 +383,7 @@ def run_gpu(args, wl, taps):
         h_out.copy_(y, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = distributed.max_over_ranks(e0.elapsed_time(e1))
 
     if rank == 0:
         pk, pk_kind = peaks()

@@ -59,8 +59,14 @@ class PostMFMSE(torch.nn.Module):
 
 def adam_fit(model, x_rx, loss_fn, iters: int = 200, lr_taps: float = 1e-2,
              lr_ratio: float = 1e-2) -> List[float]:
-    """Adam on the taps (learning rate relative to their largest magnitude) and the ratio."""
+    """Adam on the taps (learning rate relative to their largest magnitude) and the ratio.
+
+    Under torch.distributed each rank passes its own realizations (equal counts); the gradients
+    are averaged over ranks in FP64 before every update, so all ranks keep identical taps and the
+    update is the one of the whole data set.  The returned losses are the rank's own."""
+    from . import distributed
     scale = float(model.taps.detach().abs().max())
+    scale = distributed.max_over_ranks(scale)                 # the same learning rate everywhere
     opt = torch.optim.Adam([{"params": [model.taps], "lr": lr_taps * scale},
                             {"params": [model.ratio], "lr": lr_ratio}],
                            betas=(0.9, 0.999))
@@ -69,6 +75,7 @@ def adam_fit(model, x_rx, loss_fn, iters: int = 200, lr_taps: float = 1e-2,
         opt.zero_grad(set_to_none=True)
         loss = loss_fn(model(x_rx))
         loss.backward()
+        distributed.average_gradients_([model.taps, model.ratio])
         opt.step()
         losses.append(float(loss.detach()))
     return losses
