@@ -184,11 +184,15 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
             float2 u[E];
             load_ckpt(1 + s, u);
             float* prow = prow0 + gi * a.pstride;
+            // both lanes of an x/y pair hold every slot's intensity after the shuffle: lane p
+            // stores the slots t with t % 2 == p (no branch on the polarization)
 #pragma unroll
-            for (int t = 0; t < E; ++t) {
-                float pw = fmaf(u[t].x, u[t].x, u[t].y * u[t].y);
-                pw += __shfl_xor_sync(0xffffffffu, pw, 1);
-                if (p == 0) row_store<NP, E>(prow, mb, j + TPF * t, a.H, pw);
+            for (int t2 = 0; t2 < E; t2 += 2) {
+                float pw0 = fmaf(u[t2].x, u[t2].x, u[t2].y * u[t2].y);
+                float pw1 = fmaf(u[t2 + 1].x, u[t2 + 1].x, u[t2 + 1].y * u[t2 + 1].y);
+                pw0 += __shfl_xor_sync(0xffffffffu, pw0, 1);
+                pw1 += __shfl_xor_sync(0xffffffffu, pw1, 1);
+                row_store<NP, E>(prow, mb, j + TPF * (t2 + p), a.H, p ? pw1 : pw0);
             }
         }
         __syncthreads();
@@ -247,9 +251,11 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
                 const float2 v = c_mul(u[t], make_float2(1.0f + ps.x, ps.y));
                 float gt = -(x[t].x * v.y - x[t].y * v.x);                 // -Im(conj(G_v) v)
                 gt += __shfl_xor_sync(0xffffffffu, gt, 1);
-                if (p == 0) {
-                    row_store<NP, E>(trow, mb, j + TPF * t, a.H, gt);
-                    gtplain[gi * NP + j + TPF * t] = gt;
+                // both lanes hold the sum: lane p stores the odd or even slots (no branch on p)
+                if ((t & 1) == p) {
+                    const int n = j + TPF * t;
+                    row_store<NP, E>(trow, mb, n, a.H, gt);
+                    gtplain[gi * NP + n] = gt;
                 }
                 // conj(psi) G_v (the ratio path adds G_v back in the spectral domain as NP G_W)
                 x[t] = rho ? c_mulc(x[t], ps) : c_mulc(x[t], make_float2(1.0f + ps.x, ps.y));

@@ -447,33 +447,51 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
             // offsets; the halo (H <= NP/E) can only meet slots 0 and E - 1.
             constexpr bool kFlat = (E == 16) && (TPF % 64 == 0);
             const bool flat = kFlat && a.H <= TPF;
-            float* pbase = prow + pswz<E>(mb + j);
             const int dstride = PERPOL ? a.n_sb * a.pstride : 0;     // D rows follow P rows
+            // After the shuffle both lanes of an x/y pair hold |x|^2 + |y|^2 of every slot, so
+            // lane p stores the slots t with t % 2 == p: one store instruction per two slots and
+            // no branch on the polarization inside the unrolled loop.  The storing lane's D value
+            // (|x|^2 - |y|^2, per-polarization form) takes its sign from p.
+            auto slot_pair = [&](int t2, float& pw, float& dv) {   // values of slot t2 + p
+                const float own0 = fmaf(x[t2].x, x[t2].x, x[t2].y * x[t2].y);
+                const float own1 = fmaf(x[t2 + 1].x, x[t2 + 1].x, x[t2 + 1].y * x[t2 + 1].y);
+                const float oth0 = __shfl_xor_sync(0xffffffffu, own0, 1);
+                const float oth1 = __shfl_xor_sync(0xffffffffu, own1, 1);
+                pw = p == 0 ? own0 + oth0 : oth1 + own1;
+                dv = p == 0 ? own0 - oth0 : oth1 - own1;
+            };
+            if (flat) {
+                float* const pbase = prow + pswz<E>(mb + j) + TPF * p;
 #pragma unroll
-            for (int t = 0; t < E; ++t) {
-                const float own = fmaf(x[t].x, x[t].x, x[t].y * x[t].y);
-                const float oth = __shfl_xor_sync(0xffffffffu, own, 1);
-                const float pw = own + oth;                          // |x|^2 + |y|^2
-                if (p == 0) {
-                    const int n = j + TPF * t;
-                    const float dv = own - oth;                      // |x|^2 - |y|^2
-                    if (flat) {
-                        pbase[TPF * t] = pw;
-                        if constexpr (PERPOL) pbase[TPF * t + dstride] = dv;
-                        if (t == 0 && n < a.H) {
-                            prow[pswz<E>(mb + n + NP)] = pw;
-                            if constexpr (PERPOL) prow[pswz<E>(mb + n + NP) + dstride] = dv;
-                        }
-                        if (t == E - 1 && n >= NP - a.H) {
-                            prow[pswz<E>(mb + n - NP)] = pw;
-                            if constexpr (PERPOL) prow[pswz<E>(mb + n - NP) + dstride] = dv;
-                        }
-                    } else {
+                for (int t2 = 0; t2 < E; t2 += 2) {
+                    float pw, dv;
+                    slot_pair(t2, pw, dv);
+                    pbase[TPF * t2] = pw;
+                    if constexpr (PERPOL) pbase[TPF * t2 + dstride] = dv;
+                    // the halo can only meet slot 0 (lane 0 at t2 = 0) and slot E - 1 (lane 1)
+                    if (t2 == 0 && p == 0 && j < a.H) {
+                        prow[pswz<E>(mb + j + NP)] = pw;
+                        if constexpr (PERPOL) prow[pswz<E>(mb + j + NP) + dstride] = dv;
+                    }
+                    if (t2 == E - 2 && p == 1 && j + TPF * (E - 1) >= NP - a.H) {
+                        prow[pswz<E>(mb + j + TPF * (E - 1) - NP)] = pw;
+                        if constexpr (PERPOL) prow[pswz<E>(mb + j + TPF * (E - 1) - NP) + dstride] = dv;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < E; ++t) {
+                    const float own = fmaf(x[t].x, x[t].x, x[t].y * x[t].y);
+                    const float oth = __shfl_xor_sync(0xffffffffu, own, 1);
+                    if (p == 0) {
+                        const int n = j + TPF * t;
+                        const float pw = own + oth;                  // |x|^2 + |y|^2
                         prow[pswz<E>(mb + n)] = pw;
                         // circular halo: H <= NP (ntaps <= NP/2), so one copy per side suffices
                         if (n < a.H) prow[pswz<E>(mb + n + NP)] = pw;
                         if (n >= NP - a.H) prow[pswz<E>(mb + n - NP)] = pw;
                         if constexpr (PERPOL) {
+                            const float dv = own - oth;              // |x|^2 - |y|^2
                             prow[pswz<E>(mb + n) + dstride] = dv;
                             if (n < a.H) prow[pswz<E>(mb + n + NP) + dstride] = dv;
                             if (n >= NP - a.H) prow[pswz<E>(mb + n - NP) + dstride] = dv;
