@@ -10,19 +10,18 @@
 // after the last GVD.  cbessfm_grad then walks each block backwards, one CTA slot per block:
 //
 //   G_X = DEMUX(DFT_N(G_out on the kept samples))                 (adjoint of MUX + IDFT)
-//   ratio term of the last GVD:   -kdisp * Im(conj(G_X) X_final) summed over bins
 //   for s = N_st-1 .. 0:
-//     G_Y = conj(T_s) G_X ; G_v = IDFT_unnorm(G_Y)                (adjoint of T_s DFT)
-//     recompute u_s (checkpoint), P = |x|^2 + |y|^2, theta, v = u exp(j theta)
-//     G_theta_i[k] = -Im(sum_pol conj(G_v) v)
+//     G_W = conj(T_s) G_X ; G_v = IDFT_unnorm(G_W)                (adjoint of T_s DFT)
+//     recompute u_s (checkpoint), P = |x|^2 + |y|^2, theta, psi = exp(j theta) - 1
+//     G_theta_i[k] = -Im(sum_pol conj(G_v) v),  v = u (1 + psi)
 //     dL/dw[s][i][l][m] = sum_k G_theta_i[k] P_l[k - m]          (per-block partial)
 //     G_P_l[n] = sum_i sum_m w[s][i][l][m] G_theta_i[n + m]       (FIR with transposed taps)
-//     G_u = exp(-j theta) G_v + 2 G_P u ;  G_X = DFT_unnorm(G_u)
-//   ratio term of the first GVD:  +kdisp * Im(conj(G_X) X_0)
+//     G_X = NP G_W + DFT_unnorm(conj(psi) G_v + 2 G_P u)          (= DFT_unnorm(G_u))
+//     the step's term of dL/drho from D_Z = DFT(psi u) and that last DFT (see the kernel)
 //   G_in = IDFT_unnorm_N(MUX(conj(T_first) G_X))                  (adjoint of T_first DEMUX DFT)
 //
 // Per-block partial tap gradients (FP32) are summed over blocks in FP64 by a second kernel; the
-// splitting-ratio terms are accumulated in FP64 throughout.
+// splitting-ratio terms are summed per thread in FP32 and over threads and blocks in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -76,6 +75,9 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     __shared__ float2 s_rot[kRotTable];
     const ThreadPos tp = thread_pos<NP>(a.n_sb);
     for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
+    // FFT twiddles staged after the G block regions
+    float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)a.G * a.region_bytes);
+    for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(a.fft_tw + k);
     const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
     const int N = a.N, n_sb = a.n_sb;
 
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
 #pragma unroll
     for (int t = 0; t < E; ++t) x[t] = stage[2 * (n_sb * (j + TPF * t) + gi) + p];
     __syncthreads();
-    fft_regs<NP, E, false>(x, j, e, a.fft_tw, bar);
+    fft_regs<NP, E, false, true>(x, j, e, s_tw, bar);
     bar();
 #pragma unroll
     for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = x[t];
@@ -146,7 +148,14 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     }
     __syncthreads();
     // x now holds G for the spectrum after the last GVD.
-    const float* kd = a.kdisp + (size_t)gi * NP;
+    // kdisp of slot t: 2 pi^2 beta2 L_step (R/N)^2 (2 c_i k' + k'^2), k' the centred lowpass bin
+    // (the table value of the plan, with the integer part exact in FP32)
+    auto kappa = [&](int t) {
+        const int kap = j + TPF * t;
+        const int kp = kap < NP / 2 ? kap : kap - NP;
+        const int cc = -a.N / 2 + gi * NP + NP / 2;
+        return a.kd0 * (float)(2 * cc * kp + kp * kp);
+    };
     // Splitting-ratio gradient.  With Q(Z) = sum_bins kdisp Im(conj(G_Z) Z), the ratio enters
     // the first and the last GVD only, so dL/drho = Q(Z_0) - Q(Z_N) (Z_s: spectrum entering step
     // s, Z_N the final one).  Q is unchanged by a GVD, so the difference telescopes into one
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
 #pragma unroll
                     for (int t = 0; t < E; ++t) x[t] = c_conj(c_mul(cs_mine[cpad(j + TPF * t)], u[t]));
                 }
-                fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);
+                fft_regs<NP, E, true, true>(x, j, e, s_tw, bar);
                 if (ph == 0) {
                     float rs = 0.f;
 #pragma unroll
@@ -233,7 +242,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
                         const float2 zs = c_sub(c_scale(c_mulc(z1[o], hv), NPf), c_scale(dz, inv_NP));
                         if (real) sz[o] = zs;
                         const float2 gw = sg[o];
-                        rs = fmaf(-ldg_once(kd + j + TPF * t), gw.x * dz.y - gw.y * dz.x, rs);
+                        rs = fmaf(-kappa(t), gw.x * dz.y - gw.y * dz.x, rs);
                         x[t] = gw;
                     }
                     rho_part += (double)rs;
@@ -379,14 +388,14 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
         __syncthreads();
         for (int k = rem; k < n_acc; k += TB) accw[k] = 0.f;
         // D_G = DFT(conj(psi) G_v + 2 G_P u); G for Z_s = NP G_W + D_G; the D_G part of the ratio
-        fft_regs<NP, E, false>(x, j, e, a.fft_tw, bar);
+        fft_regs<NP, E, false, true>(x, j, e, s_tw, bar);
         if (rho) {
             float rs = 0.f;
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int o = 2 * (j + TPF * t);
                 const float2 zs = sz[o];
-                rs = fmaf(ldg_once(kd + j + TPF * t), x[t].x * zs.y - x[t].y * zs.x, rs);
+                rs = fmaf(kappa(t), x[t].x * zs.y - x[t].y * zs.x, rs);
                 const float2 gw = sg[o];
                 x[t] = make_float2(fmaf(NPf, gw.x, x[t].x), fmaf(NPf, gw.y, x[t].y));
             }
@@ -429,7 +438,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
         }
     }
     __syncthreads();
-    fft_regs<NP, E, true>(x, j, e, a.fft_tw, bar);
+    fft_regs<NP, E, true, true>(x, j, e, s_tw, bar);
     if (real) {
         long long pos = base % a.L;
         if (pos < 0) pos += a.L;
@@ -504,10 +513,11 @@ cudaError_t launch_np_adj(const ChainArgs& a, int threads, cudaStream_t st) {
     if (grid <= 0) return cudaSuccess;
     const size_t smem = (size_t)a.G * a.region_bytes;
     if constexpr (ADJ) {
+        const size_t smem_a = smem + chain_tw_bytes(fft_tw_size(NP));   // + staged twiddles
         cudaError_t e = cudaFuncSetAttribute(cbessfm_adj_kernel<NP>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
         if (e != cudaSuccess) return e;
-        cbessfm_adj_kernel<NP><<<(unsigned)grid, threads, smem, st>>>(a);
+        cbessfm_adj_kernel<NP><<<(unsigned)grid, threads, smem_a, st>>>(a);
     } else {
         const size_t smem_f = smem + a.tbl_bytes;        // + the chain's per-CTA tables
         cudaError_t e = cudaFuncSetAttribute(cbessfm_fwd_ckpt_kernel<NP>,
@@ -585,7 +595,7 @@ cbessfm_status check_common(const cbessfm_plan* plan, int64_t n_samples, int bat
     if (ws_bytes < l.total)
         return fail(CBESSFM_ERR_INVALID_ARG, "workspace of %zu bytes is smaller than %zu", ws_bytes, l.total);
     if (l.n_blk > (1ll << 31) - 1) return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks");
-    if (adj_region_bytes(*p) > kMaxDynSmem)
+    if (adj_region_bytes(*p) + chain_tw_bytes(fft_tw_size(p->n_fft)) > kMaxDynSmem)
         return fail(CBESSFM_ERR_UNSUPPORTED, "the adjoint of a %d-sample block does not fit shared memory",
                     p->N);
     *pp = p;
@@ -658,7 +668,6 @@ cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, doub
     a.gpart = reinterpret_cast<float*>(ws + l.ckpt_bytes + l.stash_bytes);
     a.gout = static_cast<const float2*>(grad_out);
     a.gin = static_cast<float2*>(grad_in);
-    a.kdisp = p->d_kdisp;
     a.want_ratio = grad_ratio != nullptr ? 1 : 0;
     a.taps_t = p->d_taps_t;
     // the adjoint's own region and CTA shape
@@ -666,8 +675,13 @@ cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, doub
     a.nlpr_off = round_up_i(16LL * xpad_len(p->N), 128);
     const int tpf = p->n_fft / fft_slots(p->n_fft);
     const int tb = 2 * p->n_sb * tpf;
-    a.G = choose_blocks_per_cta(tb, a.region_bytes, tpf, p->n_sb);
+    a.G = choose_blocks_per_cta(tb, a.region_bytes, tpf, p->n_sb,
+                                chain_tw_bytes(fft_tw_size(p->n_fft)));
     if (a.G < 1) return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape for the adjoint");
+    {
+        const double rn = p->link.sample_rate / p->N;
+        a.kd0 = (float)(2.0 * 9.86960440108935861883 * p->link.beta2 * p->step_length * rn * rn);
+    }
     cudaError_t e = cudaSuccess;
     if (grad_in != nullptr)
         e = cudaMemsetAsync(grad_in, 0, (size_t)n_samples * batch * 16, cs);

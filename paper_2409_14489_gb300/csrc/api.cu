@@ -53,7 +53,6 @@ int round_up(int v, int m) { return (v + m - 1) / m * m; }
 void free_plan(PlanImpl& p) {
     cudaFree(p.d_gvd);
     cudaFree(p.d_gvd_half);
-    cudaFree(p.d_kdisp);
     cudaFree(p.d_mix_tw);
     cudaFree(p.d_fft_tw);
     cudaFree(p.d_taps);
@@ -62,7 +61,6 @@ void free_plan(PlanImpl& p) {
     cudaFree(p.d_status);
     p.d_gvd = nullptr;
     p.d_gvd_half = nullptr;
-    p.d_kdisp = nullptr;
     p.d_mix_tw = nullptr;
     p.d_fft_tw = nullptr;
     p.d_taps = nullptr;
@@ -320,7 +318,6 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     } while (0)
     CB_TRY(cudaMalloc(&p.d_gvd, sizeof(float2) * 3 * bands * n_fft), "cudaMalloc(gvd)");
     CB_TRY(cudaMalloc(&p.d_gvd_half, sizeof(float2) * 4 * (p.N / 2 + 1)), "cudaMalloc(gvd half)");
-    CB_TRY(cudaMalloc(&p.d_kdisp, sizeof(float) * bands * n_fft), "cudaMalloc(kdisp)");
     CB_TRY(cudaMalloc(&p.d_mix_tw, sizeof(float2) * mix_tw.size()), "cudaMalloc(mix)");
     CB_TRY(cudaMalloc(&p.d_fft_tw, sizeof(float2) * fft_tw.size()), "cudaMalloc(fft tw)");
     CB_TRY(cudaMalloc(&p.d_taps, sizeof(float) * n_taps_dev), "cudaMalloc(taps)");

@@ -33,9 +33,9 @@ __global__ void build_gvd_half_kernel(float2* __restrict__ half, long long N, do
     half[idx] = make_float2((float)(cs * sc), (float)(sn * sc));
 }
 
-__global__ void build_gvd_kernel(float2* __restrict__ gvd, float* __restrict__ kdisp, int n_sb,
-                                 int np, double beta2, double rate, double dz0, double dz1,
-                                 double dz2, double scale0, double scale12, double step_len) {
+__global__ void build_gvd_kernel(float2* __restrict__ gvd, int n_sb, int np, double beta2,
+                                 double rate, double dz0, double dz1, double dz2, double scale0,
+                                 double scale12) {
     const int per = n_sb * np;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= 3 * per) return;
@@ -54,14 +54,6 @@ __global__ void build_gvd_kernel(float2* __restrict__ gvd, float* __restrict__ k
     sincospi(2.0 * frac, &sn, &cs);
     const double sc = tbl == 0 ? scale0 : scale12;
     gvd[idx] = make_float2((float)(cs * sc), (float)(sn * sc));
-    // d(phase)/d(ratio) weight of the splitting-ratio gradient, less the subband-centre part:
-    // a constant per subband multiplies Im<G_i, Z_i>, which every step leaves unchanged (the
-    // chain commutes with a phase rotation of one subband), so it cancels exactly in the
-    // gradient and only adds rounding error.
-    if (tbl == 0 && kdisp != nullptr) {
-        const double fc = (double)(-N / 2 + (long long)i * np + np / 2) * rate / (double)N;
-        kdisp[r] = (float)(2.0 * 9.86960440108935861883 * beta2 * step_len * (f * f - fc * fc));
-    }
 }
 
 cudaError_t launch_build_gvd(const PlanImpl& p, cudaStream_t stream) {
@@ -78,8 +70,8 @@ cudaError_t launch_build_gvd(const PlanImpl& p, cudaStream_t stream) {
     }
     const int total = 3 * p.n_sb * np;
     build_gvd_kernel<<<(total + 255) / 256, 256, 0, stream>>>(
-        p.d_gvd, p.d_kdisp, p.n_sb, np, p.link.beta2, p.link.sample_rate, dz0, dz1, dz2,
-        1.0 / (double)p.N, 1.0 / (double)np, Ls);
+        p.d_gvd, p.n_sb, np, p.link.beta2, p.link.sample_rate, dz0, dz1, dz2, 1.0 / (double)p.N,
+        1.0 / (double)np);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long half = 4LL * (p.N / 2 + 1);

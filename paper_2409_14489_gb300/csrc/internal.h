@@ -51,13 +51,13 @@ struct ChainArgs {
     const float2* rot_tbl;       // [256] exp(j 2 pi k / 256)
     unsigned int* status;        // device status word
     float2* ckpt;                // adjoint checkpoints (checkpointed forward only), else null
-    const float* kdisp;          // [n_sb][NP] 2 pi^2 beta2 L_step (f^2 - f_i^2) (adjoint only)
     const float* taps_t;         // [n_st][n_sb][n_sb][ntaps_pad] transposed, reversed taps (adjoint)
     const float2* gout;          // adjoint: dL/d(out) as (re, im) pairs, [batch][L][2]
     float2* gin;                 // adjoint: dL/d(in), accumulated, or null
     float* gpart;                // adjoint: per-block partial tap and ratio gradients
     float2* stash;               // adjoint: per-block scratch, two fields [2][gi][idx][p]
     int want_ratio;              // adjoint: 1 if dL/drho is requested
+    float kd0;                   // adjoint: 2 pi^2 beta2 L_step (R/N)^2 (ratio-gradient weights)
 };
 
 struct PlanImpl {
@@ -73,7 +73,6 @@ struct PlanImpl {
     double step_length = 0.0;
     float2* d_gvd = nullptr;      // [3][n_sb][NP]
     float2* d_gvd_half = nullptr; // [4][N/2 + 1]
-    float* d_kdisp = nullptr;     // [n_sb][NP] 2 pi^2 beta2 L_step (f^2 - f_i^2) (ratio derivative)
     float2* d_mix_tw = nullptr;   // [n_sb][N]
     float2* d_fft_tw = nullptr;
     float* d_taps = nullptr;      // [n_st][n_sb][n_sb][ntaps_pad]
