@@ -117,7 +117,9 @@ __device__ __forceinline__ int cpad(int k) { return k + (k >> 4); }
 // of four-tap chunks at compile time: one window of 8 + 4 NCH samples per row then serves all
 // chunks.  NCH = 0 handles any chunk count with one 12-sample window per chunk.
 // WS: the taps `wbase` are in shared memory (plain loads) instead of global memory.
-template <int E, int NCH, bool WS = false>
+// PAD1: the last 4-tap chunk holds one zero pad tap (ntaps = 4 NCH - 1, e.g. 11): its
+// multiply-adds are skipped (adding 0 * P leaves the sum unchanged bit for bit).
+template <int E, int NCH, bool WS = false, bool PAD1 = false>
 __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restrict__ wbase,
                                      const float* __restrict__ rows0, int k0, float (&acc)[8],
                                      int skip_l = -1) {
@@ -148,7 +150,7 @@ __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restric
                     t = fmaf(w4[c].x, win[off + q + 3], t);   // m = -nc + 4c
                     t = fmaf(w4[c].y, win[off + q + 2], t);   // m = -nc + 4c + 1
                     t = fmaf(w4[c].z, win[off + q + 1], t);
-                    t = fmaf(w4[c].w, win[off + q], t);
+                    if (!(PAD1 && c == NCH - 1)) t = fmaf(w4[c].w, win[off + q], t);
                     acc[q] = t;
                 }
             }
@@ -185,7 +187,10 @@ __device__ __forceinline__ void fir8_any(const ChainArgs& a, const float* __rest
                                          const float4* __restrict__ s_taps, int s, int i, int k0,
                                          float (&acc)[8], int skip_l) {
     if (a.taps_smem) {
-        fir8<E, 3, true>(a, s_taps + i * a.n_sb * 3, rows0, k0, acc, skip_l);   // 9 to 12 taps
+        if (a.ntaps_pad == 2 * a.nc + 2)                                     // 11 taps
+            fir8<E, 3, true, true>(a, s_taps + i * a.n_sb * 3, rows0, k0, acc, skip_l);
+        else                                                                 // 9, 10, 12 taps
+            fir8<E, 3, true>(a, s_taps + i * a.n_sb * 3, rows0, k0, acc, skip_l);
     } else {
         const float4* wbase = reinterpret_cast<const float4*>(
             a.taps + (size_t)(s * a.n_sb + i) * a.n_sb * a.ntaps_pad);
