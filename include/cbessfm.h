@@ -244,6 +244,31 @@ cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int st
                                      int grid, double* taps, double* response);
 
 /*
+ * cbessfm_backpropagate_host -- cbessfm_backpropagate of fields in host memory, with the
+ * transfers overlapped.  The batch is copied into `dev_in` in groups of realizations (at most 64
+ * groups) on a host-to-device stream; the chain kernel runs on `stream` in launches of
+ * `launch_blocks` OLS blocks of the flattened (realization, block) list, each launch waiting
+ * only for the groups it reads; each group is copied from `dev_out` to `host_out` on a
+ * device-to-host stream once its last block is computed.  Both copy streams are owned by the
+ * plan (created at the first call).  The paper has no counterpart; the chain and its result are
+ * those of cbessfm_backpropagate, bit for bit.
+ *   host_in, host_out  [batch][n_samples] samples in the plan's storage type; page-locked
+ *                      memory (cudaHostAlloc / pinned tensors) lets the copies overlap.
+ *   dev_in, dev_out    device buffers of the same size (caller-owned, must not overlap).
+ *   launch_blocks      OLS blocks per launch, rounded up to whole CTAs of the plan; 0 = one
+ *                      wave (the device's SM count times the CTAs resident per SM), which
+ *                      keeps every launch's last wave full.
+ * Asynchronous: completion is ordered on `stream` (synchronize it before reading host_out).
+ * Calls on one plan are serialized on the host; concurrent calls with one plan wait for each
+ * other's enqueueing, not for the device.  Errors: CBESSFM_ERR_INVALID_ARG for NULL buffers,
+ * n_samples or batch < 1, launch_blocks < 0, or realizations that do not span a multiple of
+ * 16 bytes (batch > 1); the checks of cbessfm_backpropagate otherwise.
+ */
+cbessfm_status cbessfm_backpropagate_host(cbessfm_plan* plan, const void* host_in, void* host_out,
+                                          void* dev_in, void* dev_out, int64_t n_samples,
+                                          int batch, int launch_blocks, cbessfm_stream stream);
+
+/*
  * Streamed form (per-step overlap-and-save).  The chain's operators are regrouped into one
  * pass per step over the whole sequence: pass s runs [GVD((1 - rho) L_step), for s = 0 only],
  * the step's NLPR, and GVD(L_step) (GVD(rho L_step) for the last step), each pass with its own

@@ -91,6 +91,9 @@ def _load():
     lib.cbessfm_backpropagate_streamed.argtypes = [P, c_void_p, c_void_p, c_void_p, ctypes.c_size_t,
                                                    c_int64, c_int, c_void_p]
     lib.cbessfm_backpropagate_streamed.restype = c_int
+    lib.cbessfm_backpropagate_host.argtypes = [P, c_void_p, c_void_p, c_void_p, c_void_p,
+                                               c_int64, c_int, c_int, c_void_p]
+    lib.cbessfm_backpropagate_host.restype = c_int
     lib.cbessfm_set_nlpr_mode.argtypes = [P, c_int]
     lib.cbessfm_set_nlpr_mode.restype = c_int
     lib.cbessfm_analytic_taps.argtypes = [ctypes.POINTER(LinkStruct), c_int, c_int, c_int,
@@ -273,6 +276,23 @@ class Plan:
         c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float32))
         _check(_lib.cbessfm_set_coeffs(self._h, c.ctypes.data, 0, _stream_handle(stream)))
         return c
+
+    def backpropagate_host(self, h_in, h_out, d_in, d_out, launch_blocks: int = 0, stream=None):
+        """Host-resident fields with overlapped transfers (``cbessfm_backpropagate_host``):
+        ``h_in``/``h_out`` pinned CPU tensors, ``d_in``/``d_out`` CUDA tensors of the same shape;
+        ``launch_blocks`` OLS blocks per kernel launch (0: one wave of the device).  Completion is
+        ordered on ``stream`` (the current stream by default)."""
+        for t in (h_in, h_out):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("h_in/h_out must be contiguous host tensors")
+        for t in (d_in, d_out):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("d_in/d_out must be contiguous CUDA tensors")
+        batch, L = self._shape(h_in)
+        _check(_lib.cbessfm_backpropagate_host(self._h, h_in.data_ptr(), h_out.data_ptr(),
+                                               d_in.data_ptr(), d_out.data_ptr(), L, batch,
+                                               launch_blocks, _stream_handle(stream)))
+        return h_out
 
     def streamed_workspace_size(self, n_samples: int, batch: int = 1) -> int:
         n = ctypes.c_size_t()

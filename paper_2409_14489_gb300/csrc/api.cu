@@ -14,9 +14,6 @@
 #include "device_common.cuh"
 #include "internal.h"
 
-struct cbessfm_plan {
-    cbessfm::PlanImpl impl;
-};
 
 namespace cbessfm {
 namespace {
@@ -218,6 +215,45 @@ const PlanImpl* plan_impl(const cbessfm_plan* plan) { return plan ? &plan->impl 
 
 using namespace cbessfm;
 
+namespace cbessfm {
+
+cbessfm_status forward_range(const cbessfm_plan* plan, const void* in, void* out,
+                             int64_t n_samples, int batch, int cta0, int n_ctas,
+                             cbessfm_stream stream) {
+    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
+    if (n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples must be >= 1");
+    if (batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "batch must be >= 1");
+    const PlanImpl& p = plan->impl;
+    const unsigned long long sample_bytes = p.storage == CBESSFM_C64 ? 16ull : 8ull;
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u)
+        return fail(CBESSFM_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
+    const unsigned long long bytes = (unsigned long long)n_samples * batch * sample_bytes;
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
+    if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
+    const long long n_blocks = (n_samples + p.V - 1) / p.V;
+    if (n_blocks * batch > (1ll << 31) - 1)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
+    const long long ctas = (n_blocks * batch + p.G - 1) / p.G;
+    if (cta0 < 0 || n_ctas < 0 || cta0 > ctas)
+        return fail(CBESSFM_ERR_INVALID_ARG, "CTA range %d + %d outside the batch's %lld", cta0,
+                    n_ctas, ctas);
+    if (cta0 == ctas) return CBESSFM_OK;
+    ChainArgs a = make_chain_args(p);
+    a.in = in;
+    a.out = out;
+    a.L = n_samples;
+    a.batch = batch;
+    a.n_blocks = (int)n_blocks;
+    a.cta0 = cta0;
+    a.n_ctas = n_ctas;
+    const cudaError_t e = launch_forward(p, a, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+    return CBESSFM_OK;
+}
+
+}  // namespace cbessfm
+
 extern "C" {
 
 const char* cbessfm_last_error(void) { return cbessfm::last_error_text(); }
@@ -358,6 +394,7 @@ cbessfm_status cbessfm_plan_destroy(cbessfm_plan* plan) {
     if (plan == nullptr) return CBESSFM_OK;
     cudaDeviceSynchronize();
     free_plan(plan->impl);
+    destroy_host_pipeline(plan->pipe);
     delete plan;
     return CBESSFM_OK;
 }
@@ -400,29 +437,7 @@ cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_strea
 cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, void* out,
                                      int64_t n_samples, int batch, cbessfm_stream stream) {
     clear_error();
-    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
-    if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
-    if (n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples must be >= 1");
-    if (batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "batch must be >= 1");
-    const PlanImpl& p = plan->impl;
-    const unsigned long long sample_bytes = p.storage == CBESSFM_C64 ? 16ull : 8ull;
-    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u)
-        return fail(CBESSFM_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
-    const unsigned long long bytes = (unsigned long long)n_samples * batch * sample_bytes;
-    const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
-    if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
-    const long long n_blocks = (n_samples + p.V - 1) / p.V;
-    if (n_blocks * batch > (1ll << 31) - 1)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
-    ChainArgs a = make_chain_args(p);
-    a.in = in;
-    a.out = out;
-    a.L = n_samples;
-    a.batch = batch;
-    a.n_blocks = (int)n_blocks;
-    const cudaError_t e = launch_forward(p, a, reinterpret_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "forward launch");
-    return CBESSFM_OK;
+    return forward_range(plan, in, out, n_samples, batch, 0, 0, stream);
 }
 
 // Streamed form: one launch of the chain per step, each with one NLPR step and its own

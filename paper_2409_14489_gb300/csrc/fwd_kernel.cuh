@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
     mbar_fence_init();
     __syncthreads();
     const long long total = (long long)a.batch * a.n_blocks;
-    const long long item = (long long)blockIdx.x * a.G + tp.g;
+    const long long item = (long long)(a.cta0 * a.G + blockIdx.x * a.G + tp.g);  // < 2^31
     const bool real = item < total;
     const int seq = real ? (int)(item / a.n_blocks) : 0;
     const int blk = real ? (int)(item % a.n_blocks) : 0;
@@ -678,7 +678,9 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_persistent_kernel(
 template <int NP, int ST>
 cudaError_t fwd_launch(const ChainArgs& a, int threads, cudaStream_t stream) {
     const long long total = (long long)a.batch * a.n_blocks;
-    const long long grid = (total + a.G - 1) / a.G;
+    const long long ctas = (total + a.G - 1) / a.G;
+    long long grid = ctas - a.cta0;
+    if (a.n_ctas > 0 && a.n_ctas < grid) grid = a.n_ctas;
     if (grid <= 0) return cudaSuccess;
     const size_t smem = (size_t)a.G * a.region_bytes + a.tbl_bytes;
     if constexpr (ST == 0) {

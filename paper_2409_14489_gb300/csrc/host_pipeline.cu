@@ -1,0 +1,177 @@
+// host_pipeline.cu -- backpropagation of host-resident fields with the transfers overlapped.
+//
+// A receiver's samples usually arrive in host memory.  cbessfm_backpropagate_host copies the
+// batch in by groups of realizations on one copy stream, runs the chain kernel in launches of
+// whole waves of OLS blocks on the caller's stream, and copies each group out on a second copy
+// stream as soon as the launches holding its last block have finished.  A launch waits only for
+// the copies of the realizations its blocks read, so the time approaches the larger of the
+// kernel time and the transfer time plus one group's copy in and out.  Launches are cut at
+// multiples of the device's resident blocks (one wave of CTAs), not at realization boundaries:
+// a launch of one realization's blocks would leave most SMs idle in its last wave.  The copy
+// streams and events belong to the plan and are created at the first call.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <new>
+
+#include "internal.h"
+
+namespace cbessfm {
+
+constexpr int kMaxCopyGroups = 64;
+
+struct HostPipeline {
+    std::mutex mu;                    // one pipelined call per plan at a time
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t start = nullptr, end = nullptr, computed = nullptr;
+    cudaEvent_t copied[kMaxCopyGroups] = {};
+    int n_sm = 0;                     // SM count of the plan's device
+};
+
+void destroy_host_pipeline(HostPipeline* hp) {
+    if (hp == nullptr) return;
+    if (hp->h2d) cudaStreamDestroy(hp->h2d);
+    if (hp->d2h) cudaStreamDestroy(hp->d2h);
+    if (hp->start) cudaEventDestroy(hp->start);
+    if (hp->end) cudaEventDestroy(hp->end);
+    if (hp->computed) cudaEventDestroy(hp->computed);
+    for (int k = 0; k < kMaxCopyGroups; ++k)
+        if (hp->copied[k]) cudaEventDestroy(hp->copied[k]);
+    delete hp;
+}
+
+namespace {
+
+std::mutex g_create_mu;
+
+cudaError_t create_pipeline(HostPipeline* hp, int device) {
+    const unsigned flags = cudaEventDisableTiming;
+    cudaError_t e = cudaDeviceGetAttribute(&hp->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->d2h, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->start, flags);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->end, flags);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->computed, flags);
+    for (int k = 0; e == cudaSuccess && k < kMaxCopyGroups; ++k)
+        e = cudaEventCreateWithFlags(&hp->copied[k], flags);
+    return e;
+}
+
+}  // namespace
+}  // namespace cbessfm
+
+using namespace cbessfm;
+
+extern "C" {
+
+cbessfm_status cbessfm_backpropagate_host(cbessfm_plan* plan, const void* host_in, void* host_out,
+                                          void* dev_in, void* dev_out, int64_t n_samples,
+                                          int batch, int launch_blocks, cbessfm_stream stream) {
+    clear_error();
+    if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
+    if (!host_in || !host_out || !dev_in || !dev_out)
+        return fail(CBESSFM_ERR_INVALID_ARG, "host_in/host_out/dev_in/dev_out is NULL");
+    if (n_samples < 1 || batch < 1 || launch_blocks < 0)
+        return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1, launch_blocks >= 0");
+    const PlanImpl& p = plan->impl;
+    const size_t sample_bytes = p.storage == CBESSFM_C64 ? 16 : 8;
+    const size_t per_seq = (size_t)n_samples * sample_bytes;
+    if ((per_seq & 15) && batch > 1)
+        return fail(CBESSFM_ERR_INVALID_ARG, "each realization must span a multiple of 16 bytes");
+    const long long n_blocks = (n_samples + p.V - 1) / p.V;
+    if (n_blocks * batch > (1ll << 31) - 1)
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
+    const int total = (int)(n_blocks * batch);
+    const uintptr_t di = reinterpret_cast<uintptr_t>(dev_in), dO = reinterpret_cast<uintptr_t>(dev_out);
+    if ((di | dO) & 15u) return fail(CBESSFM_ERR_INVALID_ARG, "dev_in/dev_out must be 16-byte aligned");
+    if (di < dO + per_seq * batch && dO < di + per_seq * batch)
+        return fail(CBESSFM_ERR_ALIAS, "dev_out overlaps dev_in");
+    {
+        std::lock_guard<std::mutex> lk(g_create_mu);
+        if (plan->pipe == nullptr) {
+            HostPipeline* hp = new (std::nothrow) HostPipeline;
+            if (hp == nullptr) return fail(CBESSFM_ERR_OOM, "host allocation of the pipeline failed");
+            const cudaError_t e = create_pipeline(hp, p.device);
+            if (e != cudaSuccess) {
+                destroy_host_pipeline(hp);
+                return cuda_fail(e, "pipeline streams/events");
+            }
+            plan->pipe = hp;
+        }
+    }
+    HostPipeline& hp = *plan->pipe;
+    std::lock_guard<std::mutex> call_lock(hp.mu);
+    // CTAs per launch: one wave of resident CTAs unless the caller fixes the blocks per launch
+    // (rounded up to whole CTAs of G blocks)
+    int wave = hp.n_sm * (resident_blocks(p.G, p.threads / p.G, p.region_bytes, p.tbl_bytes) / p.G);
+    if (wave < 1) wave = 1;
+    const int per_launch = launch_blocks > 0 ? (launch_blocks + p.G - 1) / p.G : wave;
+    const int n_ctas = (total + p.G - 1) / p.G;
+    // copy groups of `cg` realizations (at most kMaxCopyGroups groups)
+    const int cg = (batch + kMaxCopyGroups - 1) / kMaxCopyGroups;
+    const int n_groups = (batch + cg - 1) / cg;
+
+    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaEventRecord(hp.start, st);              // after the caller's earlier work
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.h2d, hp.start, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.d2h, hp.start, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
+    const unsigned char* hin = static_cast<const unsigned char*>(host_in);
+    unsigned char* hout = static_cast<unsigned char*>(host_out);
+    unsigned char* din = static_cast<unsigned char*>(dev_in);
+    unsigned char* dout = static_cast<unsigned char*>(dev_out);
+    auto group_span = [&](int g, size_t* off, size_t* bytes) {
+        const int r0 = g * cg, r1 = r0 + cg < batch ? r0 + cg : batch;
+        *off = (size_t)r0 * per_seq;
+        *bytes = (size_t)(r1 - r0) * per_seq;
+        return r1;                                              // one past the group's last realization
+    };
+    for (int g = 0; g < n_groups; ++g) {                        // the copy engine runs them in order
+        size_t off, bytes;
+        group_span(g, &off, &bytes);
+        e = cudaMemcpyAsync(din + off, hin + off, bytes, cudaMemcpyHostToDevice, hp.h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(hp.copied[g], hp.h2d);
+        if (e != cudaSuccess) return cuda_fail(e, "pipeline copy in");
+    }
+    int waited = -1, out_next = 0;                              // groups waited for / copied out
+    for (int c0 = 0; c0 < n_ctas; c0 += per_launch) {
+        const int nc = n_ctas - c0 > per_launch ? per_launch : n_ctas - c0;
+        const int i1 = (c0 + nc) * p.G < total ? (c0 + nc) * p.G : total;   // items [c0 G, i1)
+        const int g_in = (int)((i1 - 1) / n_blocks) / cg;       // last group the launch reads
+        if (g_in > waited) {
+            e = cudaStreamWaitEvent(st, hp.copied[g_in], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "pipeline wait for copy in");
+            waited = g_in;
+        }
+        const cbessfm_status s = forward_range(plan, din, dout, n_samples, batch, c0, nc, stream);
+        if (s != CBESSFM_OK) return s;
+        // groups whose every block is now computed go out in one copy
+        int g_end = out_next;
+        while (g_end < n_groups) {
+            size_t off, bytes;
+            const int r1 = group_span(g_end, &off, &bytes);
+            if ((long long)r1 * n_blocks > i1) break;
+            ++g_end;
+        }
+        if (g_end > out_next) {
+            size_t off0, b0, off1, b1;
+            group_span(out_next, &off0, &b0);
+            group_span(g_end - 1, &off1, &b1);
+            // the wait binds to this record; later records of the event do not affect it
+            e = cudaEventRecord(hp.computed, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.d2h, hp.computed, 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hout + off0, dout + off0, off1 + b1 - off0,
+                                    cudaMemcpyDeviceToHost, hp.d2h);
+            if (e != cudaSuccess) return cuda_fail(e, "pipeline copy out");
+            out_next = g_end;
+        }
+    }
+    e = cudaEventRecord(hp.end, hp.d2h);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, hp.end, 0);   // completion on `stream`
+    if (e != cudaSuccess) return cuda_fail(e, "pipeline end");
+    return CBESSFM_OK;
+}
+
+}  // extern "C"

@@ -58,6 +58,9 @@ struct ChainArgs {
     float2* stash;               // adjoint: per-block scratch, two fields [2][gi][idx][p]
     int want_ratio;              // adjoint: 1 if dL/drho is requested
     float kd0;                   // adjoint: 2 pi^2 beta2 L_step (R/N)^2 (ratio-gradient weights)
+    int cta0, n_ctas;            // forward launch over CTAs [cta0, cta0 + n_ctas) of the whole
+                                 // batch's grid (n_ctas = 0: to the end); CTA c runs work items
+                                 // c G .. c G + G - 1, item = seq * n_blocks + blk
 };
 
 struct PlanImpl {
@@ -118,6 +121,33 @@ const char* last_error_text();
 
 // The plan object behind the opaque C handle.
 const PlanImpl* plan_impl(const cbessfm_plan* plan);
+
+// OLS blocks resident per SM for G blocks of `tb` threads per CTA, `region` bytes each, and
+// `tables` bytes of per-CTA tables.
+int resident_blocks(int G, int tb, int region, int tables);
+
+// cbessfm_backpropagate restricted to the CTAs [cta0, cta0 + n_ctas) of the whole batch's grid
+// (n_ctas = 0: to the end), i.e. the work items [cta0 G, (cta0 + n_ctas) G) of the flattened
+// (sequence, block) list, item = seq * n_blocks + blk, with G = the plan's blocks per CTA.  The
+// blocks of the range read their input (with its overlap, which wraps within the sequence) and
+// write their valid samples only.
+cbessfm_status forward_range(const cbessfm_plan* plan, const void* in, void* out,
+                             int64_t n_samples, int batch, int cta0, int n_ctas,
+                             cbessfm_stream stream);
+
+// Streams and events of cbessfm_backpropagate_host, created on first use, owned by the plan.
+struct HostPipeline;
+void destroy_host_pipeline(HostPipeline* hp);
+
+}  // namespace cbessfm
+
+// The object behind the opaque C handle.
+struct cbessfm_plan {
+    cbessfm::PlanImpl impl;
+    cbessfm::HostPipeline* pipe = nullptr;   // streams and events of the host-pipelined entry
+};
+
+namespace cbessfm {
 
 // Persistent batched launch of the forward kernel for one (NP, storage) group.
 cudaError_t launch_forward_persistent(int np, int storage, const ChainArgs* jobs, const int2* items,
