@@ -67,6 +67,11 @@ def test_invalid_link_and_null_arguments(lib):
     assert lib.lib().cbessfm_plan_create(None, 1, 0, 0.5, None, 1, 64, 16, 0,
                                          ctypes.byref(h)) == lib.ERR_INVALID_ARG
     assert lib.lib().cbessfm_backpropagate(None, None, None, 10, 1, None) == lib.ERR_INVALID_ARG
+    assert lib.lib().cbessfm_backpropagate_host(None, None, None, None, None, 10, 1, 0,
+                                                None) == lib.ERR_INVALID_ARG
+    assert lib.lib().cbessfm_backpropagate_streamed(None, None, None, None, 0, 10, 1,
+                                                    None) == lib.ERR_INVALID_ARG
+    assert lib.lib().cbessfm_set_nlpr_mode(None, 1) == lib.ERR_INVALID_ARG
     assert lib.lib().cbessfm_plan_destroy(None) == lib.OK
 
 
