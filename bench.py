@@ -254,6 +254,60 @@ def form_adjoint(steps: int, warmup: int):
             "gpu_launches_per_step": 4}
 
 
+def form_precision(plan_c64, taps, x_c64, steps: int, warmup: int):
+    """Precision form: the c2 launch with FP16 and BF16 storage (FP32 arithmetic), and the c5
+    long-haul workload (N' = 2048, 40 steps) with complex64 and FP16 storage.  Reports each
+    launch time and the rel-L2 of the 16-bit output against the complex64 output of the same
+    launch (the oracle comparison is in the tests)."""
+    import torch
+    from paper_2409_14489_gb300 import cbessfm
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+    out = {}
+    wl = configs.get_workload(WORKLOAD)
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    y64 = plan_c64.backpropagate(x_c64)
+    x4 = torch.view_as_real(x_c64).reshape(x_c64.shape[0], x_c64.shape[1], 4)
+    ref4 = torch.view_as_real(y64).reshape(x4.shape)
+    for name, st, dt in (("c2_fp16_storage", cbessfm.STORAGE_F16X4, torch.float16),
+                         ("c2_bf16_storage", cbessfm.STORAGE_BF16X4, torch.bfloat16)):
+        plan = cbessfm.Plan(plan_c64.link, d.n_sb, d.n_st, d.ratio, taps.astype(np.float32),
+                            d.n_fft, d.overlap, storage=st)
+        xs = x4.to(dt).contiguous()
+        t = _events_ms(lambda: plan.backpropagate(xs), steps, warmup)
+        ys = plan.backpropagate(xs).float()
+        out[name] = {"ms_per_step": t, "value": wl.batch * sig.sym2d_per_realization / (t / 1e3),
+                     "unit": UNIT, "rel_l2_vs_complex64": rel(ys, ref4),
+                     "bytes_per_launch": 2 * xs.numel() * xs.element_size()}
+    # c5: one realization, N' = 2048
+    w5 = configs.get_workload("c5_longhaul")
+    d5, lk5, sig5 = w5.dbp, w5.link, w5.signal
+    w0 = lk5.gamma * signals.effective_length(lk5.alpha, lk5.span_length)
+    taps5 = signals.random_taps(w5.seed, d5.n_st, d5.n_sb, d5.ntaps, w0, spread=0.2)
+    f5, _ = signals.tx_waveform(w5, w5.launch_dbm[0], seed=w5.seed * 1000 + 7)
+    link5 = cbessfm.make_link(lk5.beta2, lk5.span_length, lk5.n_spans, sig5.sample_rate)
+    x5 = torch.from_numpy(f5.astype(np.complex64)[None]).cuda()
+    p5 = cbessfm.Plan(link5, d5.n_sb, d5.n_st, d5.ratio, taps5.astype(np.float32), d5.n_fft,
+                      d5.overlap)
+    t5 = _events_ms(lambda: p5.backpropagate(x5), steps, warmup)
+    y5 = p5.backpropagate(x5)
+    p5h = cbessfm.Plan(link5, d5.n_sb, d5.n_st, d5.ratio, taps5.astype(np.float32), d5.n_fft,
+                       d5.overlap, storage=cbessfm.STORAGE_F16X4)
+    x5h = torch.view_as_real(x5).reshape(1, -1, 4).half().contiguous()
+    t5h = _events_ms(lambda: p5h.backpropagate(x5h), steps, warmup)
+    y5h = p5h.backpropagate(x5h).float()
+    sym5 = sig5.sym2d_per_realization
+    out["c5_complex64"] = {"ms_per_step": t5, "value": sym5 / (t5 / 1e3), "unit": UNIT,
+                           "workload": "c5_longhaul: 5 ch x 64 GBd, 40x80 km, N_sb=5, N_st=40, "
+                                       "N'=2048, N'_ov=512, 1 x 1,310,720 samples"}
+    out["c5_fp16_storage"] = {"ms_per_step": t5h, "value": sym5 / (t5h / 1e3), "unit": UNIT,
+                              "rel_l2_vs_complex64": rel(y5h, torch.view_as_real(y5).reshape(1, -1, 4))}
+    out["gpu_launches_per_step"] = 1
+    return out
+
+
 def _oracle_blocks(field, p, d, n_blocks, first, stride, budget_s):
     """Run the FP64 oracle (mode B) on blocks first, first + stride, ... of one realization for
     about ``budget_s`` seconds; returns (blocks done, seconds)."""
@@ -310,34 +364,68 @@ def cpu_baseline(wl, taps, fields, budget_s: float = 12.0):
     return value, cores, single, desc
 
 
+_REF_STATE = {}
+
+
+def _ref_init(field, taps64):
+    """Spawn-pool initializer of the reference arm: the realization and the chain parameters."""
+    from oracle import dbp as odbp
+    wl = configs.get_workload(WORKLOAD)
+    d, lk, sig = wl.dbp, wl.link, wl.signal
+    _REF_STATE["field"] = field
+    _REF_STATE["p"] = odbp.ChainParams(beta2=lk.beta2, sample_rate=sig.sample_rate,
+                                       link_length=lk.length, n_sb=d.n_sb, ratio=d.ratio,
+                                       taps=taps64)
+
+
+def _ref_blocks(blocks):
+    """Reference-arm worker: the FP64 oracle (mode B) on the given blocks of the realization."""
+    from oracle import dbp as odbp
+    d = configs.get_workload(WORKLOAD).dbp
+    odbp.dbp_mode_b(_REF_STATE["field"], _REF_STATE["p"], d.n_fft, d.overlap, blocks=list(blocks))
+    return len(blocks)
+
+
 def run_reference(args, wl, taps):
+    """The reference arm: the FP64 oracle as it stands, on every host core (one spawned process
+    per core), each step a bounded sample of the workload: blocks_per_core whole blocks per
+    process."""
+    import multiprocessing
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     fields = workload_inputs(wl)[:1]
-    from oracle import dbp as odbp
-    d, lk, sig = wl.dbp, wl.link, wl.signal
-    p = odbp.ChainParams(beta2=lk.beta2, sample_rate=sig.sample_rate, link_length=lk.length,
-                         n_sb=d.n_sb, ratio=d.ratio, taps=taps.astype(np.float32).astype(np.float64))
+    d, sig = wl.dbp, wl.signal
     V = d.n_block - d.n_ov_total
     n_blocks = -(-sig.n_samples // V)
-    blocks_per_step = 4
     sym_per_sample = sig.sym2d_per_realization / sig.n_samples
-    f = fields[0].astype(np.complex128)
-    for w in range(args.warmup):
-        odbp.dbp_mode_b(f, p, d.n_fft, d.overlap, blocks=[w % n_blocks])
-    t0 = time.perf_counter()
-    for k in range(args.steps):
-        odbp.dbp_mode_b(f, p, d.n_fft, d.overlap,
-                        blocks=[(k * blocks_per_step + i) % n_blocks for i in range(blocks_per_step)])
-    el = time.perf_counter() - t0
-    value = args.steps * blocks_per_step * V * sym_per_sample / el
-    sample = f"{blocks_per_step} overlap-and-save blocks ({V} valid samples each) per step"
+    cores = os.cpu_count() or 1
+    blocks_per_core = 2
+    per_step = cores * blocks_per_core
+    taps64 = taps.astype(np.float32).astype(np.float64)
+    field = fields[0].astype(np.complex128)
+
+    def step_jobs(k):
+        b0 = k * per_step
+        return [[(b0 + c * blocks_per_core + i) % n_blocks for i in range(blocks_per_core)]
+                for c in range(cores)]
+
+    with multiprocessing.get_context("spawn").Pool(cores, initializer=_ref_init,
+                                                   initargs=(field, taps64)) as pool:
+        for w in range(args.warmup):
+            pool.map(_ref_blocks, step_jobs(w), chunksize=1)
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            pool.map(_ref_blocks, step_jobs(args.warmup + k), chunksize=1)
+        el = time.perf_counter() - t0
+    value = args.steps * per_step * V * sym_per_sample / el
+    sample = (f"{per_step} overlap-and-save blocks ({V} valid samples each) per step, "
+              f"{blocks_per_core} per process on {cores} processes")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(wl),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -458,6 +546,10 @@ def run_gpu(args, wl, taps):
             forms["adjoint"] = form_adjoint(max(3, min(args.steps, 10)), 2)
         except Exception as exc:
             forms["adjoint"] = {"error": repr(exc)}
+        try:
+            forms["precision"] = form_precision(plan, taps, x, max(3, min(args.steps, 10)), 2)
+        except Exception as exc:
+            forms["precision"] = {"error": repr(exc)}
         try:
             # the same c2 launch with the full-complexity per-polarization NLPR (Eqs. NLPR_polx/poly)
             plan.set_nlpr_mode(True)
