@@ -188,7 +188,7 @@ def form_batched(steps: int, warmup: int):
     tuner = autotune.Autotuner("model")
     w0 = lk.gamma * signals.effective_length(lk.alpha, lk.span_length)
     link = cbessfm.make_link(lk.beta2, lk.span_length, lk.n_spans, sig.sample_rate)
-    jobs, sym2d = [], 0
+    jobs, sym2d, flops = [], 0, 0.0
     for k, jb in enumerate(signals.batch_jobs_c3(wl.seed)):
         n_fft, ov = tuner.choose(autotune.JobShape(jb["n_sb"], jb["n_st"], d.ntaps, lk.beta2,
                                                    lk.length, sig.sample_rate))
@@ -200,6 +200,10 @@ def form_batched(steps: int, warmup: int):
         x = torch.from_numpy(tx.astype(np.complex64)).cuda()
         jobs.append((plan, x, torch.empty_like(x)))
         sym2d += w.signal.sym2d_per_realization
+        # the paper's RM + RA of this job (its own N, overlap and step count)
+        n_per4d = w.signal.n_samples / (w.signal.sym2d_per_realization / 2.0)
+        flops += w.signal.sym2d_per_realization * cost.cbessfm_flops_per_2d(
+            jb["n_sb"] * n_fft, jb["n_sb"] * ov, n_per4d, jb["n_sb"], jb["n_st"])
     batch = cbessfm.Batch(jobs)
     graph = batch.capture()
     t_graph = _events_ms(graph.replay, steps, warmup)
@@ -209,6 +213,7 @@ def form_batched(steps: int, warmup: int):
                         " subbands {1,3,5}, autotuned N' / overlap",
             "value": sym2d / (t_graph / 1e3), "unit": UNIT, "ms_per_step": t_graph,
             "sym2d_per_step": sym2d, "groups": info["groups"], "work_items": info["work_items"],
+            "algorithmic_tflops": flops / (t_graph / 1e3) / 1e12,
             "gpu_launches_per_step": info["groups"],
             "plain_launches": {"value": sym2d / (t_plain / 1e3), "ms_per_step": t_plain,
                                "gpu_launches_per_step": len(jobs)},
@@ -542,6 +547,8 @@ def run_gpu(args, wl, taps):
             forms["batched"] = form_batched(max(3, min(args.steps, 10)), 2)
         except Exception as exc:                       # report, do not lose the main line
             forms["batched"] = {"error": repr(exc)}
+        if "algorithmic_tflops" in forms["batched"]:
+            forms["batched"]["frac_of_fp32_peak"] = forms["batched"]["algorithmic_tflops"] / fp32_peak
         try:
             forms["adjoint"] = form_adjoint(max(3, min(args.steps, 10)), 2)
         except Exception as exc:
