@@ -329,12 +329,24 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
                 fft_tw[off + (r - 1) * NS + a] = make_float2((float)std::cos(ang), (float)std::sin(ang));
             }
     }
-    std::vector<float2> mix_tw((size_t)bands * p.N);
+    // [bands][N] W_N^(K r), then the per-slot factors of the chain's DEMUX and MUX:
+    // [bands][E] W_N^(r (N'/E) t) times W_N^(-r N') for t >= E/2 (DEMUX), [bands][E] W_N^(r (N'/E) t)
+    const int E = fft_slots(n_fft), TPF = n_fft / E;
+    std::vector<float2> mix_tw((size_t)bands * p.N + 2 * (size_t)bands * E);
+    auto w_n = [&](long long num) {                  // W_N^num, exponent reduced exactly mod N
+        num %= p.N;
+        if (num < 0) num += p.N;
+        const double ang = -two_pi * (double)num / (double)p.N;
+        return make_float2((float)std::cos(ang), (float)std::sin(ang));
+    };
     for (int r = 0; r < bands; ++r)
-        for (int K = 0; K < p.N; ++K) {
-            const long long num = ((long long)K * r) % p.N;
-            const double ang = -two_pi * (double)num / (double)p.N;
-            mix_tw[(size_t)r * p.N + K] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        for (int K = 0; K < p.N; ++K) mix_tw[(size_t)r * p.N + K] = w_n((long long)K * r);
+    float2* const mix_td = mix_tw.data() + (size_t)bands * p.N;
+    float2* const mix_tm = mix_td + (size_t)bands * E;
+    for (int r = 0; r < bands; ++r)
+        for (int t = 0; t < E; ++t) {
+            mix_td[r * E + t] = w_n((long long)r * (TPF * t - (t >= E / 2 ? n_fft : 0)));
+            mix_tm[r * E + t] = w_n((long long)r * TPF * t);
         }
 
     std::vector<float2> rot(256);

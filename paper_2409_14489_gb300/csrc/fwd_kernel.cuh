@@ -397,19 +397,25 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     const int ci = -N / 2 + gi * NP + NP / 2;                      // centre bin of subband gi
     {
         // X_i[kap] = sum_r W_N^(K r) Y_r[K mod NP], K = (c_i + k') mod N; loop r outermost so that
-        // only the E accumulators stay live.
+        // only the E accumulators stay live.  With K_0 = c_i + j (slot 0), K = K_0 + (N'/E) t, less
+        // N' for t >= E/2, so W_N^(K r) = W_N^(K_0 r) times a factor of (r, t) only: one table
+        // load per r and thread, the factors from a small table read alike by the whole warp.
         const float2* eb = reinterpret_cast<const float2*>(region) + p;
+        const float2* td = a.mix_tw + (size_t)a.n_sb * N;                 // [n_sb][E]
+        int K0 = ci + j;
+        K0 += (K0 < 0) ? N : 0;
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
         for (int r = 0; r < a.n_sb; ++r) {
             const float2* er = eb + r * XL;
-            const float2* wr = a.mix_tw + (size_t)r * N;
+            const float2 w0 = __ldg(a.mix_tw + (size_t)r * N + K0);        // W_N^(K_0 r)
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int kap = j + TPF * t;
                 int K = ci + (kap < NP / 2 ? kap : kap - NP);
                 K += (K < 0) ? N : 0;
-                x[t] = c_add(x[t], c_mul(er[2 * xpad(K & (NP - 1))], __ldg(wr + K)));
+                const float2 w = c_mul(w0, __ldg(td + r * E + t));
+                x[t] = c_add(x[t], c_mul(er[2 * xpad(K & (NP - 1))], w));
             }
         }
     }
@@ -547,15 +553,19 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
             ex[2 * xpad(K)] = x[t];
         }
         __syncthreads();
-        // Z_r[kap] = sum_q conj(W_N^(K r)) Xi[K], K = kap + NP q (q outermost, as above)
+        // Z_r[kap] = sum_q conj(W_N^(K r)) Xi[K], K = kap + NP q (q outermost, as above), with
+        // W_N^(K r) = W_N^((j + NP q) r) W_N^((N'/E) t r): one table load per q and thread
         const float2* wr = a.mix_tw + (size_t)gi * N;
+        const float2* tm = a.mix_tw + (size_t)a.n_sb * (N + E) + gi * E;   // [n_sb][E], row gi
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
         for (int q = 0; q < a.n_sb; ++q) {
+            const float2 w0 = __ldg(wr + j + NP * q);
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int K = j + TPF * t + NP * q;
-                x[t] = c_add(x[t], c_mulc(ex[2 * xpad(K)], __ldg(wr + K)));
+                const float2 w = c_mul(w0, __ldg(tm + t));
+                x[t] = c_add(x[t], c_mulc(ex[2 * xpad(K)], w));
             }
         }
     }

@@ -45,7 +45,8 @@ struct ChainArgs {
                                  // unit factor (x 1/N) as kind 3
     const float2* gvd_first;     // gvd_half kind of the first GVD (kind 0, or 3 in later passes)
     const float2* gvd_last;      // gvd_half kind of the last step's GVD (kind 2, or 1)
-    const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
+    const float2* mix_tw;        // [n_sb][N]: W_N^(K r), then [n_sb][E] DEMUX and [n_sb][E] MUX
+                                 // slot factors (see the chain's DEMUX and MUX)
     const float2* fft_tw;        // FFT pass twiddles (fft_tw_size(NP))
     const float* taps;           // [n_st][n_sb][n_sb][ntaps_pad]
     const float2* rot_tbl;       // [256] exp(j 2 pi k / 256)
@@ -76,7 +77,7 @@ struct PlanImpl {
     double step_length = 0.0;
     float2* d_gvd = nullptr;      // [3][n_sb][NP]
     float2* d_gvd_half = nullptr; // [4][N/2 + 1]
-    float2* d_mix_tw = nullptr;   // [n_sb][N]
+    float2* d_mix_tw = nullptr;   // [n_sb][N] + 2 [n_sb][E]
     float2* d_fft_tw = nullptr;
     float* d_taps = nullptr;      // [n_st][n_sb][n_sb][ntaps_pad]
     float2* d_rot = nullptr;      // [256] exp(j 2 pi k / 256) from FP64
