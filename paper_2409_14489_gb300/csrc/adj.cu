@@ -131,18 +131,23 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     __syncthreads();
     const int ci = -N / 2 + gi * NP + NP / 2;
     {
+        // DEMUX as in the forward chain: W_N^(K r) = W_N^(K_0 r) times the slot factor of (r, t)
         const float2* eb = reinterpret_cast<const float2*>(region) + p;
+        const float2* td = a.mix_tw + (size_t)n_sb * N;
+        int K0 = ci + j;
+        K0 += (K0 < 0) ? N : 0;
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
         for (int r = 0; r < n_sb; ++r) {
             const float2* er = eb + r * XL;
-            const float2* wr = a.mix_tw + (size_t)r * N;
+            const float2 w0 = __ldg(a.mix_tw + (size_t)r * N + K0);
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int kap = j + TPF * t;
                 int K = ci + (kap < NP / 2 ? kap : kap - NP);
                 K += (K < 0) ? N : 0;
-                x[t] = c_add(x[t], c_mul(er[2 * xpad(K & (NP - 1))], __ldg(wr + K)));
+                const float2 w = c_mul(w0, __ldg(td + r * E + t));
+                x[t] = c_add(x[t], c_mul(er[2 * xpad(K & (NP - 1))], w));
             }
         }
     }
@@ -426,14 +431,18 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
             ex[2 * xpad(K)] = x[t];
         }
         __syncthreads();
+        // MUX as in the forward chain: W_N^(K gi) = W_N^((j + NP q) gi) W_N^((N'/E) t gi)
         const float2* wr = a.mix_tw + (size_t)gi * N;
+        const float2* tm = a.mix_tw + (size_t)n_sb * (N + E) + gi * E;
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
         for (int q = 0; q < n_sb; ++q) {
+            const float2 w0 = __ldg(wr + j + NP * q);
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int K = j + TPF * t + NP * q;
-                x[t] = c_add(x[t], c_mulc(ex[2 * xpad(K)], __ldg(wr + K)));
+                const float2 w = c_mul(w0, __ldg(tm + t));
+                x[t] = c_add(x[t], c_mulc(ex[2 * xpad(K)], w));
             }
         }
     }

@@ -372,14 +372,41 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
             return false;
         }
     } else {
-        uint2* st8 = reinterpret_cast<uint2*>(region);
+        // 8-byte samples: bulk copies when every segment starts and ends on a 16-byte boundary
+        // (even L and an even start), coalesced 8-byte loads otherwise.  Either way the slot's
+        // mbarrier completes one phase, so the persistent kernels' phase parity stays in step.
+        const bool bulk = real && ((a.L | pos0) & 1) == 0;
         const uint2* src = reinterpret_cast<const uint2*>(a.in) + (long long)seq * a.L;
-        for (int n = rem; n < a.N; n += TB) {
-            long long q = pos0 + n;
-            q -= (q / a.L) * a.L;
-            st8[n] = real ? __ldg(src + q) : make_uint2(0u, 0u);
+        uint2* st8 = reinterpret_cast<uint2*>(region);
+        if (rem == 0) {
+            if (bulk) {
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar_g, (uint32_t)a.N * 8u);
+                long long pos = pos0;
+                int dst = 0;
+                while (dst < a.N) {
+                    const int len = (int)min((long long)(a.N - dst), a.L - pos);
+                    bulk_copy_g2s(st8 + dst, src + pos, (uint32_t)len * 8u, bar_g);
+                    dst += len;
+                    pos = 0;
+                }
+            } else {
+                mbar_arrive(bar_g);
+            }
         }
-        __syncthreads();
+        if (!bulk) {
+            for (int n = rem; n < a.N; n += TB) {
+                long long q = pos0 + n;
+                q -= (q / a.L) * a.L;
+                st8[n] = real ? __ldg(src + q) : make_uint2(0u, 0u);
+            }
+        }
+        const bool ok = mbar_wait_bounded(bar_g, parity, kWaitCycles);
+        if (__syncthreads_or(!ok)) {
+            if (!ok) atomicOr(a.status, kStatusTimeout);
+            if (bulk) mbar_wait_bounded(bar_g, parity, kWaitCycles);
+            return false;
+        }
     }
 
     float2 x[E];

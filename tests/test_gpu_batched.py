@@ -55,6 +55,28 @@ def test_batched_matches_plain_launches_bitwise():
         assert plan.status() == 0
 
 
+def test_batched_16bit_storage_mixed_staging_bitwise():
+    """One persistent launch over FP16 jobs whose blocks are staged by bulk copies (even length
+    and start) and by plain loads (odd length or odd start), interleaved on the same CTAs: the
+    staging mbarrier's phases stay in step, and each job equals its plain launch."""
+    import torch
+    from paper_2409_14489_gb300 import cbessfm
+    # overlap 16: even block starts (bulk copies for an even length, a mix for an odd one);
+    # overlap 18: odd starts (plain loads)
+    cases = [Case(3, 256, ov, 2, 5, 0.3, n, sample_rate=192e9, seed=20 + k, storage=st)
+             for k, (n, st, ov) in enumerate([(4000, 1, 16), (4001, 1, 16), (6000, 1, 18),
+                                              (2999, 1, 16), (5000, 2, 16), (5001, 2, 18)])]
+    jobs = _jobs(cases)
+    batch = cbessfm.Batch([(plan, x, y) for _, _, plan, x, y in jobs])
+    batch.run()
+    torch.cuda.synchronize()
+    for c, taps, plan, x, y in jobs:
+        ref = plan.backpropagate(x)
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref), c
+        assert plan.status() == 0
+
+
 def test_batched_job_against_oracle():
     import torch
     from paper_2409_14489_gb300 import cbessfm
