@@ -276,11 +276,15 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
             }
         }
         __syncthreads();
+        // x (conj(psi) G_v) waits in this thread's own slots of the exchange array, idle until the
+        // step's last transform, so the correlation below has the registers to itself
+#pragma unroll
+        for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = x[t];
         {
             // dL/dw[s][i][l][m] = sum_k G_theta_i[k] P_l[k - m].  Each (i, l) pair is handled by
-            // 16 consecutive lanes; lane `sub` takes the 4-sample chunks k0 = 64 r + 4 sub (its
-            // float4 loads are 16 bytes apart across lanes: no bank conflicts), loads one
-            // intensity window for all 12 taps of the 9-to-12-tap case (4 + 12 - 1 samples), and
+            // 16 consecutive lanes; lane `sub` takes the KW-sample chunks k0 = 16 KW r + KW sub
+            // (its float4 loads are 16 bytes apart across lanes: no bank conflicts), loads one
+            // intensity window for all 12 taps of the 9-to-12-tap case (KW + 12 - 1 samples), and
             // accumulates the 12 tap sums in registers; a 16-lane shuffle reduction then gives
             // each pair's sums to one lane, which stores them.  Other tap counts use the generic
             // loop below.
@@ -298,15 +302,23 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
 #pragma unroll
                 for (int m = 0; m < 12; ++m) acc[m] = 0.f;
                 if (act) {
-                    for (int k0 = 4 * sub; k0 < NP; k0 += 64) {
-                        const float4 g4 = *reinterpret_cast<const float4*>(gtr + k0);
-                        const float g[4] = {g4.x, g4.y, g4.z, g4.w};
+                    constexpr int KW = NP >= 128 ? 8 : 4;           // samples per lane and pass
+#pragma unroll 2
+                    for (int it = 0; it < NP / (16 * KW); ++it) {
+                        const int k0 = KW * sub + 16 * KW * it;
+                        float g[KW];
+#pragma unroll
+                        for (int c4 = 0; c4 < KW / 4; ++c4) {
+                            const float4 g4 = *reinterpret_cast<const float4*>(gtr + k0 + 4 * c4);
+                            g[4 * c4] = g4.x; g[4 * c4 + 1] = g4.y; g[4 * c4 + 2] = g4.z;
+                            g[4 * c4 + 3] = g4.w;
+                        }
                         // P_l[k0 + q - m], m = -nc + mi (mi in [0, 12)): window start
                         // k0 + nc - 11, aligned because (H + p_off + nc + 1) % 4 == 0
                         const int ws = mb + k0 + a.nc - 11;
-                        float win[16];
+                        float win[KW + 12];
 #pragma unroll
-                        for (int e4 = 0; e4 < 4; ++e4) {
+                        for (int e4 = 0; e4 < KW / 4 + 3; ++e4) {
                             const float4 v = *reinterpret_cast<const float4*>(pr + pswz<E>(ws + 4 * e4));
                             win[4 * e4] = v.x; win[4 * e4 + 1] = v.y; win[4 * e4 + 2] = v.z;
                             win[4 * e4 + 3] = v.w;
@@ -314,7 +326,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
 #pragma unroll
                         for (int mi = 0; mi < 12; ++mi)
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) acc[mi] = fmaf(g[q], win[q - mi + 11], acc[mi]);
+                            for (int q = 0; q < KW; ++q) acc[mi] = fmaf(g[q], win[q - mi + 11], acc[mi]);
                     }
                 }
 #pragma unroll
@@ -387,7 +399,8 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const float gp2 = 2.f * gpr[j + TPF * t];
-                x[t] = make_float2(fmaf(gp2, u[t].x, x[t].x), fmaf(gp2, u[t].y, x[t].y));
+                const float2 xv = e[2 * xpad(j + TPF * t)];               // parked above
+                x[t] = make_float2(fmaf(gp2, u[t].x, xv.x), fmaf(gp2, u[t].y, xv.y));
             }
         }
         __syncthreads();
