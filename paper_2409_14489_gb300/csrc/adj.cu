@@ -197,6 +197,13 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
         {
             float2 u[E];
             load_ckpt(1 + s, u);
+            // while the FIR runs, this thread's slots of the exchange array (idle until the next
+            // transform; every earlier exchange load is done, the last barrier of the previous
+            // step's transform being behind us) keep what the transform after it needs: the
+            // step's time samples (the source of D_Z) on the ratio path, G_W otherwise (the ratio
+            // path has G_W in its scratch field)
+#pragma unroll
+            for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = rho ? u[t] : x[t];
             float* prow = prow0 + gi * a.pstride;
             // both lanes of an x/y pair hold every slot's intensity after the shuffle: lane p
             // stores the slots t with t % 2 == p (no branch on the polarization)
@@ -228,13 +235,16 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
         // G_W back into x as the second transform's input.
         {
             const float2* z1 = s == a.n_st - 1 ? ck + (size_t)(a.n_st + 1) * 2 * N : sz;
+            if (!rho) {
+#pragma unroll
+                for (int t = 0; t < E; ++t) x[t] = e[2 * xpad(j + TPF * t)];      // G_W
+            }
 #pragma unroll 1
             for (int ph = rho ? 0 : 1; ph < 2; ++ph) {
                 if (ph == 0) {
-                    float2 u[E];
-                    load_ckpt(1 + s, u);
 #pragma unroll
-                    for (int t = 0; t < E; ++t) x[t] = c_conj(c_mul(cs_mine[cpad(j + TPF * t)], u[t]));
+                    for (int t = 0; t < E; ++t)                                    // u from e
+                        x[t] = c_conj(c_mul(cs_mine[cpad(j + TPF * t)], e[2 * xpad(j + TPF * t)]));
                 }
                 fft_regs<NP, E, true, true>(x, j, e, s_tw, bar);
                 if (ph == 0) {
