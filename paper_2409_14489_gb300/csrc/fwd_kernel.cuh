@@ -1,9 +1,11 @@
 // fwd_kernel.cuh -- fused CB-ESSFM forward chain kernel (sm_103a), templated on N' and storage.
 //
 // One CTA processes G overlap-and-save blocks (Sec. III-A, Fig. 2); each block is handled by
-// n_sb groups of NP/16 threads.  Per block:
+// n_sb groups of 2 NP/E threads (one polarization per thread, E = 16 register slots, 32 for
+// N' = 2048).  Per block:
 //   1. bulk-copy (TMA) the N = n_sb * NP input samples into shared memory (two or more copies
-//      when the block wraps around the periodic sequence);
+//      when the block wraps around the periodic sequence; 8-byte samples whose segments are
+//      not 16-byte aligned are loaded by the threads instead);
 //   2. full-band DFT of size N per polarization as n_sb polyphase DFTs of size NP (group r
 //      transforms x[n_sb n' + r]) followed by the twiddled n_sb-point combination
 //      X[K] = sum_r W_N^(K r) Y_r[K mod NP], evaluated directly at the bins of each subband
@@ -441,7 +443,10 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                 const int kap = j + TPF * t;
                 int K = ci + (kap < NP / 2 ? kap : kap - NP);
                 K += (K < 0) ? N : 0;
-                const float2 w = c_mul(w0, __ldg(td + r * E + t));
+                // E = 32 (N' = 2048) keeps the plain table read: its 32 slots leave no registers
+                // for the product
+                const float2 w = E == 16 ? c_mul(w0, __ldg(td + r * E + t))
+                                         : __ldg(a.mix_tw + (size_t)r * N + K);
                 x[t] = c_add(x[t], c_mul(er[2 * xpad(K & (NP - 1))], w));
             }
         }
@@ -591,7 +596,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int K = j + TPF * t + NP * q;
-                const float2 w = c_mul(w0, __ldg(tm + t));
+                const float2 w = E == 16 ? c_mul(w0, __ldg(tm + t)) : __ldg(wr + K);   // as above
                 x[t] = c_add(x[t], c_mulc(ex[2 * xpad(K)], w));
             }
         }
