@@ -256,8 +256,9 @@ cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int st
  *                      memory (cudaHostAlloc / pinned tensors) lets the copies overlap.
  *   dev_in, dev_out    device buffers of the same size (caller-owned, must not overlap).
  *   launch_blocks      OLS blocks per launch, rounded up to whole CTAs of the plan; 0 = one
- *                      wave (the device's SM count times the CTAs resident per SM), which
- *                      keeps every launch's last wave full.
+ *                      wave (the device's SM count times the CTAs resident per SM) for the
+ *                      first launch and two waves for the later ones, which keeps every launch's
+ *                      last wave full.
  * Asynchronous: completion is ordered on `stream` (synchronize it before reading host_out).
  * Calls on one plan are serialized on the host; concurrent calls with one plan wait for each
  * other's enqueueing, not for the device.  Errors: CBESSFM_ERR_INVALID_ARG for NULL buffers,
