@@ -21,7 +21,7 @@ For that profile the paper gives the closed form (Eq. kernel_analytic)
 The double integral is evaluated as the paper suggests, from the kernel on a square grid of
 frequencies: an M x M midpoint rule, whose diagonal sums are a two-dimensional DFT of the grid.
 
-Readings taken here (listed in the design doc):
+Readings taken here (where the paper is silent or ambiguous):
 * The spans of a step start at z = -L/2 + n L_sp (the appendix places them at multiples of L_sp
   for even N_sp, which is the same grid).
 * K(mu, nu) is not Hermitian (K(mu, nu) != conj K(nu, mu)), so c_il[m] is complex in general;

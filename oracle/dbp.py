@@ -8,7 +8,7 @@ h = exp(+j 2 pi^2 beta2 dz f^2) (Sec. III-A, the inverse of Eq. (GVD_transfer-fu
 asymmetric steps (Sec. III-C) the first GVD covers (1 - rho) L_step, the interior ones L_step and
 the last one rho L_step.
 
-Readings of the paper taken here (each listed in the design doc):
+Readings of the paper taken here (where it is silent or ambiguous):
 * Subband i (0-based) owns the centred bins b in [-N/2 + i N', -N/2 + (i+1) N'); its centre is
   c_i = -N/2 + i N' + N'/2 and its lowpass samples are
   u_i[k] = (1/N) sum_{k'} X[c_i + k'] exp(+j 2 pi k' k / N'), k' in [-N'/2, N'/2), so a unit tone
