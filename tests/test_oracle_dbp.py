@@ -14,6 +14,9 @@ textbook algorithms.  None of these re-types the oracle's own code path:
   index map and the XPM coupling indices).
 * Overlap-and-save: circular-shift equivariance by V samples, and agreement with the whole-
   sequence chain when the overlap covers the channel memory.
+* Chain inversion: every operator of the chain is invertible (GVD is unitary, the rotation keeps
+  |u|^2 so its phase can be recomputed from its output), and the chain with -beta2, the ratio
+  1 - rho and the negated taps in reverse step order undoes it.
 """
 import math
 
@@ -249,3 +252,22 @@ def test_overlap_save_with_adequate_overlap_matches_whole_sequence():
     np.testing.assert_array_equal(part[:V], blocks[:V])
     np.testing.assert_array_equal(part[5 * V: 6 * V], blocks[5 * V: 6 * V])
     assert np.isnan(part[V]).all()
+
+
+@pytest.mark.parametrize("n_sb,n_st,rho", [(1, 2, 0.3), (3, 4, 0.12), (5, 3, 0.7)])
+def test_reverse_chain_undoes_the_chain(n_sb, n_st, rho):
+    """Applied in reverse, the steps of the chain are GVD(-rho L), rotation by exp(-j theta_N),
+    GVD(-L), ..., rotation by exp(-j theta_1), GVD(-(1 - rho) L).  That is the chain itself
+    with -beta2, ratio 1 - rho and taps -w[N_st - 1 - s], so running it on the output must give
+    the input back; the rotation phase is recomputed from the rotated field's own intensity."""
+    L = 96 * n_sb
+    u = _rand_field(L, scale=0.5)
+    taps = signals.random_taps(7, n_st, n_sb, 7, 0.8, spread=0.5)
+    p = dbp.ChainParams(beta2=-21.7e-27, sample_rate=64e9 * n_sb, link_length=320e3, n_sb=n_sb,
+                        ratio=rho, taps=taps)
+    inv = dbp.ChainParams(beta2=21.7e-27, sample_rate=64e9 * n_sb, link_length=320e3,
+                          n_sb=n_sb, ratio=1.0 - rho, taps=-taps[::-1].copy())
+    out = dbp.dbp_mode_u(u, p)
+    assert np.linalg.norm(out - u) > 0.1 * np.linalg.norm(u)        # the chain did something
+    back = dbp.dbp_mode_u(out, inv)
+    assert np.linalg.norm(back - u) / np.linalg.norm(u) < 1e-12
