@@ -31,6 +31,23 @@ def test_host_pipeline_equals_device_path(storage, launch_blocks):
     assert plan.status() == 0
 
 
+def test_host_pipeline_automatic_launches_span_several_waves():
+    """Two c2-sized realizations (5 subbands, N' = 1024: one resident block per SM, 342 blocks):
+    the automatic sizing runs a first launch of one wave and a second of up to two waves, and
+    the copies out follow each realization's last block."""
+    import torch
+    case = Case(5, 1024, 256, 2, 11, 0.3, 655360, batch=2, sample_rate=640e9, seed=7)
+    plan = make_plan(case, case_taps(case))
+    x = to_storage(random_field(case), 0)
+    want = plan.backpropagate(x).cpu()
+    h_in, h_out = _pinned(x)
+    d_in, d_out = torch.empty_like(x), torch.empty_like(x)
+    plan.backpropagate_host(h_in, h_out, d_in, d_out)
+    torch.cuda.synchronize()
+    assert torch.equal(h_out, want)
+    assert plan.status() == 0
+
+
 def test_host_pipeline_groups_many_realizations():
     """70 realizations (more than the 64 copy groups: two per group), 2 blocks each."""
     import torch
