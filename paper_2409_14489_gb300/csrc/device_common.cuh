@@ -88,11 +88,18 @@ __device__ __forceinline__ void dft2(float2& a0, float2& a1) {
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
     const float2 s02 = c_add(a0, a2), d02 = c_sub(a0, a2);
-    const float2 s13 = c_add(a1, a3), d13 = c_quarter<INV>(c_sub(a1, a3));
+    const float2 s13 = c_add(a1, a3), d13 = c_sub(a1, a3);
     a0 = c_add(s02, s13);
     a2 = c_sub(s02, s13);
-    a1 = c_add(d02, d13);
-    a3 = c_sub(d02, d13);
+    // d02 +- q(d13) with q = -i (forward) or +i (inverse), by components: the swapped pair
+    // q(d13) never has to be formed
+    if constexpr (INV) {
+        a1 = make_float2(d02.x - d13.y, d02.y + d13.x);
+        a3 = make_float2(d02.x + d13.y, d02.y - d13.x);
+    } else {
+        a1 = make_float2(d02.x + d13.y, d02.y - d13.x);
+        a3 = make_float2(d02.x - d13.y, d02.y + d13.x);
+    }
 }
 
 template <bool INV>
