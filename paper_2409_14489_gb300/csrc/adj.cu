@@ -197,11 +197,12 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
         {
             float2 u[E];
             load_ckpt(1 + s, u);
-            // while the FIR runs, this thread's slots of the exchange array (idle until the next
-            // transform; every earlier exchange load is done, the last barrier of the previous
-            // step's transform being behind us) keep what the transform after it needs: the
-            // step's time samples (the source of D_Z) on the ratio path, G_W otherwise (the ratio
-            // path has G_W in its scratch field)
+            // while the FIR runs, this thread's slots of the exchange array keep what the
+            // transform after it needs: the step's time samples (the source of D_Z) on the ratio
+            // path, G_W otherwise (the ratio path has G_W in its scratch field).  The array is
+            // idle until that transform, and no other thread still reads these slots: the last
+            // pass of every transform loads exactly the thread's own slot elements, and before
+            // the first step only barrier-separated DEMUX reads touched the array.
 #pragma unroll
             for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = rho ? u[t] : x[t];
             float* prow = prow0 + gi * a.pstride;
