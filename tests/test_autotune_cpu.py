@@ -1,0 +1,64 @@
+"""Host logic of the batched form's autotuner (paper_2409_14489_gb300/autotune.py), on CPU: the
+overlap covers the link's dispersion memory, the candidate list respects the block limits, the
+cost model picks the candidate with the lowest paper operation count per valid sample, and a
+cached measurement is reused without touching a GPU."""
+import json
+import math
+
+import pytest
+
+from paper_2409_14489_gb300 import autotune, cost
+
+
+def _shape(n_sb=1, n_st=1, ntaps=5, L=80e3, R=64e9):
+    return autotune.JobShape(n_sb, n_st, ntaps, -21.7e-27, L, R)
+
+
+def test_memory_and_overlap_follow_the_dispersion_spread():
+    s = _shape()
+    # |beta2| 2 pi R^2 L: about 44.7 samples for 80 km at 64 GS/s
+    want = 21.7e-27 * 2 * math.pi * 64e9 ** 2 * 80e3
+    assert autotune.memory_samples(s) == pytest.approx(want, rel=1e-12)
+    assert autotune.overlap_for(s) == 48                    # rounded up to a multiple of 16
+    assert autotune.overlap_for(_shape(n_sb=3)) == 16       # 14.9 per subband
+    assert autotune.overlap_for(_shape(n_sb=5)) == 16       # 8.9, at least 16
+    assert autotune.overlap_for(_shape(L=1200e3)) == 672    # 15 spans: 670.5 -> 672
+    for n_sb in (1, 2, 3, 5):
+        for L in (80e3, 400e3, 1200e3):
+            ov = autotune.overlap_for(_shape(n_sb=n_sb, L=L))
+            assert ov % 16 == 0 and ov * n_sb >= autotune.memory_samples(_shape(n_sb=n_sb, L=L))
+
+
+def test_candidates_respect_overlap_taps_and_block_limits():
+    s = _shape(L=1200e3)                                     # overlap 672
+    nfs = [nf for nf, _ in autotune.candidates(s)]
+    assert nfs == [1024, 2048]
+    assert all(ov == 672 for _, ov in autotune.candidates(s))
+    assert [nf for nf, _ in autotune.candidates(_shape(ntaps=601))] == [2048]
+    assert 2048 not in [nf for nf, _ in autotune.candidates(_shape(n_sb=6))]
+    # memory longer than any block: the largest block with a capped overlap
+    assert autotune.candidates(_shape(L=5000e3)) == [(2048, 1536)]
+
+
+def test_model_mode_picks_the_cheapest_candidate():
+    tuner = autotune.Autotuner("model")
+    for n_sb in (1, 3, 5):
+        for n_st in (1, 4, 15):
+            for L in (80e3, 800e3):
+                s = _shape(n_sb=n_sb, n_st=n_st, L=L, R=64e9 * n_sb)
+                nf, ov = tuner.choose(s)
+                costs = {c: autotune.model_cost(s, *c) for c in autotune.candidates(s)}
+                assert costs[(nf, ov)] == min(costs.values())
+                N, N_ov = n_sb * nf, n_sb * ov
+                assert autotune.model_cost(s, nf, ov) == cost.cbessfm_flops_per_2d(
+                    N, N_ov, 2.0, n_sb, n_st)
+
+
+def test_measured_choice_is_read_back_from_the_cache(tmp_path):
+    s = _shape(n_sb=3, n_st=4, L=80e3, R=192e9)              # overlap 144: four candidates
+    assert len(autotune.candidates(s)) == 4
+    path = tmp_path / "autotune.json"
+    path.write_text(json.dumps({s.key(): [512, 144]}))
+    tuner = autotune.Autotuner("measure", cache_path=str(path))
+    assert tuner.choose(s) == (512, 144)                    # no launch needed for a cached shape
+    assert s.key() != _shape(n_sb=3, n_st=4, L=80e3, R=192e9, ntaps=7).key()
