@@ -30,20 +30,22 @@ class PostMFMSE(torch.nn.Module):
     """MSE after matched filter, decimation to 1 sample/symbol and mean-phase removal.
 
     ``symbols``: (batch, n_sym, 2) transmitted unit-energy symbols; ``p_pol``: launch power per
-    polarization (W) so that the matched-filter output is compared at unit scale.
+    polarization (W) so that the matched-filter output is compared at unit scale; ``device``:
+    where the loss runs (the DBP output's device).
     """
 
     def __init__(self, n_samples: int, sample_rate: float, baud: float, rolloff: float,
-                 symbols, p_pol: float, ch_offset: float = 0.0):
+                 symbols, p_pol: float, ch_offset: float = 0.0, device="cuda"):
         super().__init__()
         self.sps = int(round(sample_rate / baud))
         freq = np.fft.fftfreq(n_samples, d=1.0 / sample_rate)
         g = rrc_amplitude(freq, baud, rolloff)
         t = np.arange(n_samples) / sample_rate
-        self.register_buffer("G", torch.tensor(g, dtype=torch.float32).cuda())
+        self.register_buffer("G", torch.tensor(g, dtype=torch.float32, device=device))
         self.register_buffer("shift", torch.tensor(np.exp(-2j * math.pi * ch_offset * t),
-                                                   dtype=torch.complex64).cuda())
-        self.register_buffer("x", torch.as_tensor(np.asarray(symbols), dtype=torch.complex64).cuda())
+                                                   dtype=torch.complex64, device=device))
+        self.register_buffer("x", torch.as_tensor(np.asarray(symbols), dtype=torch.complex64,
+                                                  device=device))
         self.scale = 1.0 / math.sqrt(p_pol)
 
     def forward(self, y):
