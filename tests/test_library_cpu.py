@@ -92,3 +92,31 @@ def test_analytic_taps_rejects_invalid_arguments(lib, kw, msg):
                                          args["grid"], taps.ctypes.data, None)
     assert st == lib.ERR_INVALID_ARG
     assert msg in lib.lib().cbessfm_last_error().decode()
+
+
+def test_every_entry_point_rejects_a_null_handle_without_a_device(lib):
+    """Each call that takes a plan or batch validates it before any CUDA call: a NULL handle
+    (or NULL output pointer) is INVALID_ARG with a message, never a crash; destroy(NULL) is OK."""
+    L, E, P = lib.lib(), lib, None
+    size = ctypes.c_size_t()
+    n_groups, n_items = ctypes.c_int(), ctypes.c_longlong()
+    checks = {
+        "set_coeffs": lambda: L.cbessfm_set_coeffs(P, P, 0, P),
+        "set_ratio": lambda: L.cbessfm_set_ratio(P, ctypes.c_double(0.5), P),
+        "grad_workspace_size": lambda: L.cbessfm_grad_workspace_size(P, 100, 1, ctypes.byref(size)),
+        "backpropagate_checkpointed": lambda: L.cbessfm_backpropagate_checkpointed(
+            P, P, P, 100, 1, P, 0, P),
+        "grad": lambda: L.cbessfm_grad(P, P, P, P, P, P, 0, 100, 1, P),
+        "batch_create": lambda: L.cbessfm_batch_create(P, 1, P),
+        "batch_run": lambda: L.cbessfm_batch_run(P, P),
+        "batch_info": lambda: L.cbessfm_batch_info(P, ctypes.byref(n_groups), ctypes.byref(n_items)),
+        "batch_run_noalloc": lambda: L.cbessfm_batch_run_noalloc(P, 1, P),
+        "streamed_workspace_size": lambda: L.cbessfm_streamed_workspace_size(
+            P, 100, 1, ctypes.byref(size)),
+        "get_status": lambda: L.cbessfm_get_status(P, P),
+    }
+    for name, call in checks.items():
+        st = call()
+        assert st == E.ERR_INVALID_ARG, (name, st)
+        assert L.cbessfm_last_error(), name
+    assert L.cbessfm_batch_destroy(P) == E.OK
