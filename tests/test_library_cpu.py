@@ -120,3 +120,29 @@ def test_every_entry_point_rejects_a_null_handle_without_a_device(lib):
         assert st == E.ERR_INVALID_ARG, (name, st)
         assert L.cbessfm_last_error(), name
     assert L.cbessfm_batch_destroy(P) == E.OK
+
+
+def test_plan_create_rejects_more_invalid_arguments(lib):
+    """Step count cap, a NaN ratio, an unknown storage type, missing taps and broken links."""
+    import numpy as np
+    L = lib.lib()
+    taps = np.zeros((1, 1, 1, 5), np.float32)
+    tp = taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    good = lib.make_link(-21.7e-27, 80e3, 1, 64e9)
+    h = ctypes.c_void_p()
+
+    def create(link, steps=1, ratio=0.5, coeffs=tp, storage=0):
+        return L.cbessfm_plan_create(ctypes.byref(link), 1, steps, ratio, coeffs, 5, 256, 64,
+                                     storage, ctypes.byref(h))
+
+    for kw, msg in [(dict(steps=4097), "steps"), (dict(ratio=float("nan")), "ratio"),
+                    (dict(storage=7), "storage"), (dict(coeffs=None), "coeffs")]:
+        assert create(good, **kw) == lib.ERR_INVALID_ARG, kw
+        assert msg in L.cbessfm_last_error().decode(), kw
+        assert not h.value
+    for link, msg in [(lib.make_link(-21.7e-27, 0.0, 1, 64e9), "span_length"),
+                      (lib.make_link(-21.7e-27, 80e3, 0, 64e9), "span_length"),
+                      (lib.make_link(float("inf"), 80e3, 1, 64e9), "beta2"),
+                      (lib.make_link(-21.7e-27, 80e3, 1, float("nan")), "sample_rate")]:
+        assert create(link) == lib.ERR_INVALID_ARG, msg
+        assert msg in L.cbessfm_last_error().decode(), msg
