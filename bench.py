@@ -73,6 +73,20 @@ def recorded_traffic():
     return float(m_tr.group(1))
 
 
+def recorded_ncu_counters():
+    """FP32-pipe and issue utilization of the same ncu capture as the traffic, if it matches
+    the current source (None otherwise)."""
+    if recorded_traffic() is None:
+        return None
+    txt = open(TRAFFIC_FILE).read()
+    out = {}
+    for key in ("fma_pipe_pct", "issue_active_pct", "warp_instructions"):
+        m = re.search(key + r":\s*([0-9.eE+]+)", txt)
+        if m:
+            out[key] = float(m.group(1))
+    return out or None
+
+
 def workload_setup():
     wl = configs.get_workload(WORKLOAD)
     d, lk, sig = wl.dbp, wl.link, wl.signal
@@ -591,6 +605,7 @@ def run_gpu(args, wl, taps):
             "roofline": {
                 "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": recorded_traffic(),
+                "ncu": recorded_ncu_counters(),
                 "peak_source": (f"FP32: {N_SM} SMs x {FP32_LANES} lanes x 2 flop x "
                                 f"{sm_mhz:g} MHz ({pk_kind} max SM clock)"),
                 "flops_per_launch": flops_launch,

@@ -35,3 +35,19 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_recorded_counters_follow_the_kernel_source_hash(tmp_path, monkeypatch):
+    """roofline.traffic and roofline.ncu come from the committed capture only while the kernel
+    sources still hash to the value recorded with it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    f = tmp_path / "traffic.txt"
+    body = ("source_hash: {h}\ndram_bytes_per_full_launch: 123\nfma_pipe_pct: 50.5\n"
+            "issue_active_pct: 60.0\n")
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    f.write_text(body.format(h=bench.kernel_source_hash()))
+    assert bench.recorded_traffic() == 123.0
+    assert bench.recorded_ncu_counters() == {"fma_pipe_pct": 50.5, "issue_active_pct": 60.0}
+    f.write_text(body.format(h="0" * 16))
+    assert bench.recorded_traffic() is None and bench.recorded_ncu_counters() is None
