@@ -332,6 +332,12 @@ class Plan:
             _lib.cbessfm_plan_destroy(self._h)
             self._h = ctypes.c_void_p()
 
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
     def __del__(self):
         try:
             self.close()
@@ -384,6 +390,12 @@ class Batch:
         if self._h:
             _lib.cbessfm_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
     def __del__(self):
         try:

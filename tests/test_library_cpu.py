@@ -146,3 +146,17 @@ def test_plan_create_rejects_more_invalid_arguments(lib):
                       (lib.make_link(-21.7e-27, 80e3, 1, float("nan")), "sample_rate")]:
         assert create(link) == lib.ERR_INVALID_ARG, msg
         assert msg in L.cbessfm_last_error().decode(), msg
+
+
+def test_plan_and_batch_close_idempotently_as_context_managers(lib):
+    """Plan and Batch release their handle on leaving a `with` block; close() on a released (NULL)
+    handle is a no-op, so an explicit close inside the block and __del__ afterwards are safe."""
+    for cls in (lib.Plan, lib.Batch):
+        obj = object.__new__(cls)
+        obj._h = ctypes.c_void_p()
+        with obj as same:
+            assert same is obj
+            obj.close()
+        assert not obj._h.value
+        obj.close()
+        obj.__del__()
