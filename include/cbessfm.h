@@ -46,7 +46,7 @@ typedef enum {
     CBESSFM_ERR_UNSUPPORTED = 2,     /* valid, but not supported by this build (size limits)   */
     CBESSFM_ERR_ALIAS = 3,           /* output overlaps input                                  */
     CBESSFM_ERR_CUDA = 4,            /* a CUDA runtime call failed                             */
-    CBESSFM_ERR_OOM = 5,             /* device or host allocation failed                       */
+    CBESSFM_ERR_OOM = 5,             /* device or host allocation (or a host resource) failed  */
     CBESSFM_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up (see get_status)    */
     CBESSFM_ERR_NOT_IMPLEMENTED = 7
 } cbessfm_status;

@@ -8,27 +8,25 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
-#include <string>
 #include <vector>
 
 #include "device_common.cuh"
+#include "abi_guard.h"
 #include "internal.h"
 
 
 namespace cbessfm {
 namespace {
 
-thread_local std::string g_last_error;
+thread_local char g_last_error[512];   // fixed size: reporting an error never allocates
 
 }  // namespace
 
 cbessfm_status fail(cbessfm_status st, const char* fmt, ...) {
-    char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof(buf), fmt, ap);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
     va_end(ap);
-    g_last_error = buf;
     return st;
 }
 
@@ -37,8 +35,8 @@ cbessfm_status cuda_fail(cudaError_t e, const char* what) {
                 cudaGetErrorString(e));
 }
 
-void clear_error() { g_last_error.clear(); }
-const char* last_error_text() { return g_last_error.c_str(); }
+void clear_error() { g_last_error[0] = '\0'; }
+const char* last_error_text() { return g_last_error; }
 
 namespace {
 
@@ -110,20 +108,22 @@ bool choose_layout(PlanImpl& p, int tb, int tpf) {
     struct Cand {
         int layout, region, nlpr_off, exb_off, pbuf;
     };
-    std::vector<Cand> cands;
+    // in order of preference; index k is the layout the override name names[k] selects
+    Cand cands[4];
     if (p.per_pol) {
         // the Px - Py rows take the second intensity buffer (one intensity buffer, so the
-        // barrier after the FIR spans the CTA)
-        cands.push_back({kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, 0});
-        cands.push_back({kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, 0});
-        cands.push_back({kLayoutSeparate, exch + 2 * prow + csr, exch, 0, 0});
-        cands.push_back({kLayoutAlias, round_up(std::max(exch, 2 * prow + csr), 128), 0, 0, 0});
+        // barrier after the FIR spans the CTA); there is no one-buffer ping-pong form, so
+        // "pingpong1" selects the same layout as "pingpong2"
+        cands[0] = {kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, 0};
+        cands[1] = cands[0];
+        cands[2] = {kLayoutSeparate, exch + 2 * prow + csr, exch, 0, 0};
+        cands[3] = {kLayoutAlias, round_up(std::max(exch, 2 * prow + csr), 128), 0, 0, 0};
     } else {
         // ping-pong exchange arrays with two intensity buffers, then with one
-        cands.push_back({kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, prow});
-        cands.push_back({kLayoutPingPong, 2 * exch + prow, 2 * exch, exch, 0});
-        cands.push_back({kLayoutSeparate, exch + prow + csr, exch, 0, 0});
-        cands.push_back({kLayoutAlias, round_up(std::max(exch, prow + csr), 128), 0, 0, 0});
+        cands[0] = {kLayoutPingPong, 2 * exch + 2 * prow, 2 * exch, exch, prow};
+        cands[1] = {kLayoutPingPong, 2 * exch + prow, 2 * exch, exch, 0};
+        cands[2] = {kLayoutSeparate, exch + prow + csr, exch, 0, 0};
+        cands[3] = {kLayoutAlias, round_up(std::max(exch, prow + csr), 128), 0, 0, 0};
     }
     // Optional override of the automatic choice (tuning): CBESSFM_SMEM_LAYOUT = pingpong2 |
     // pingpong1 | separate | alias.  A layout that does not fit falls back to the automatic one.
@@ -137,7 +137,7 @@ bool choose_layout(PlanImpl& p, int tb, int tpf) {
     const int tw = chain_tw_bytes(fft_tw_size(n_fft));
     const int tw_taps = tw + (p.nchunks == 3 ? chain_taps_bytes(bands) : 0);
     int best = -1, best_res = 0, best_G = 0, best_tbl = 0;
-    for (int k = 0; k < (int)cands.size(); ++k) {
+    for (int k = 0; k < 4; ++k) {
         const Cand& c = cands[k];
         int tbl = tw_taps;
         int G = choose_blocks_per_cta(tb, c.region, tpf, bands, tbl);
@@ -260,10 +260,9 @@ const char* cbessfm_last_error(void) { return cbessfm::last_error_text(); }
 
 const char* cbessfm_version(void) { return "cbessfm-gb300 0.1 (sm_103a)"; }
 
-cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int steps, double ratio,
-                                   const float* coeffs, int ntaps, int n_fft, int overlap,
-                                   cbessfm_storage storage, cbessfm_plan** out) {
-    clear_error();
+static cbessfm_status plan_create_body(const cbessfm_link* link, int bands, int steps,
+                                       double ratio, const float* coeffs, int ntaps, int n_fft,
+                                       int overlap, cbessfm_storage storage, cbessfm_plan** out) {
     if (out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (link == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "link is NULL");
@@ -354,6 +353,8 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
         const double ang = two_pi * k / 256.0;
         rot[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
+    // every host container exists before the first device allocation (see abi_guard.h)
+    const std::vector<float> packed = steps > 0 ? pack_taps(p, coeffs) : std::vector<float>();
 
     const size_t n_taps_dev = std::max<size_t>(1, (size_t)steps * bands * bands * p.ntaps_pad);
 #define CB_TRY(call, what)                    \
@@ -380,11 +381,9 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     CB_TRY(cudaMemcpy(p.d_mix_tw, mix_tw.data(), sizeof(float2) * mix_tw.size(),
                       cudaMemcpyHostToDevice), "copy mix twiddles");
     CB_TRY(cudaMemset(p.d_taps, 0, sizeof(float) * n_taps_dev), "cudaMemset(taps)");
-    if (steps > 0) {
-        const std::vector<float> packed = pack_taps(p, coeffs);
+    if (steps > 0)
         CB_TRY(cudaMemcpy(p.d_taps, packed.data(), sizeof(float) * packed.size(),
                           cudaMemcpyHostToDevice), "copy taps");
-    }
     CB_TRY(launch_build_gvd(p, nullptr), "build GVD tables");
     CB_TRY(launch_transpose_taps(p, nullptr), "transpose taps");
     CB_TRY(prepare_forward(n_fft, (int)storage, kMaxDynSmem), "set shared-memory limit");
@@ -401,6 +400,16 @@ cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int step
     return CBESSFM_OK;
 }
 
+cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int steps, double ratio,
+                                   const float* coeffs, int ntaps, int n_fft, int overlap,
+                                   cbessfm_storage storage, cbessfm_plan** out) {
+    clear_error();
+    return abi_guard([&] {
+        return plan_create_body(link, bands, steps, ratio, coeffs, ntaps, n_fft, overlap, storage,
+                                out);
+    });
+}
+
 cbessfm_status cbessfm_plan_destroy(cbessfm_plan* plan) {
     clear_error();
     if (plan == nullptr) return CBESSFM_OK;
@@ -411,9 +420,8 @@ cbessfm_status cbessfm_plan_destroy(cbessfm_plan* plan) {
     return CBESSFM_OK;
 }
 
-cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int on_device,
-                                  cbessfm_stream stream) {
-    clear_error();
+static cbessfm_status set_coeffs_body(cbessfm_plan* plan, const float* coeffs, int on_device,
+                                      cbessfm_stream stream) {
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     PlanImpl& p = plan->impl;
     if (p.n_st == 0) return CBESSFM_OK;
@@ -434,6 +442,12 @@ cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int o
     if (e == cudaSuccess) e = launch_transpose_taps(p, st);
     if (e != cudaSuccess) return cuda_fail(e, "set_coeffs");
     return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int on_device,
+                                  cbessfm_stream stream) {
+    clear_error();
+    return abi_guard([&] { return set_coeffs_body(plan, coeffs, on_device, stream); });
 }
 
 cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_stream stream) {
@@ -520,8 +534,7 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
     return CBESSFM_OK;
 }
 
-cbessfm_status cbessfm_set_nlpr_mode(cbessfm_plan* plan, int per_polarization) {
-    clear_error();
+static cbessfm_status set_nlpr_mode_body(cbessfm_plan* plan, int per_polarization) {
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     if (per_polarization != 0 && per_polarization != 1)
         return fail(CBESSFM_ERR_INVALID_ARG, "per_polarization must be 0 or 1");
@@ -539,6 +552,11 @@ cbessfm_status cbessfm_set_nlpr_mode(cbessfm_plan* plan, int per_polarization) {
                     p.n_sb, p.n_fft);
     p = trial;
     return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_set_nlpr_mode(cbessfm_plan* plan, int per_polarization) {
+    clear_error();
+    return abi_guard([&] { return set_nlpr_mode_body(plan, per_polarization); });
 }
 
 cbessfm_status cbessfm_get_status(const cbessfm_plan* plan, cbessfm_stream stream) {

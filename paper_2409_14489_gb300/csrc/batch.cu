@@ -15,6 +15,7 @@
 #include <tuple>
 #include <vector>
 
+#include "abi_guard.h"
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -50,8 +51,7 @@ using namespace cbessfm;
 
 extern "C" {
 
-cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_batch** out) {
-    clear_error();
+static cbessfm_status batch_create_body(const cbessfm_job* jobs, int njobs, cbessfm_batch** out) {
     if (out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (jobs == nullptr || njobs < 1) return fail(CBESSFM_ERR_INVALID_ARG, "no jobs");
@@ -83,18 +83,15 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
         by_shape[std::make_tuple(p->n_fft, p->n_sb, (int)p->storage, p->per_pol)].push_back(k);
     }
 
-    cbessfm_batch* b = new (std::nothrow) cbessfm_batch;
-    if (b == nullptr) return fail(CBESSFM_ERR_OOM, "host allocation of the batch failed");
-    b->njobs = njobs;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     int n_sm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) {
-        free_batch(b);
-        return cuda_fail(e, "device query");
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "device query");
 
+    // the groups and work items are built in host containers before the batch and its device
+    // memory exist (see abi_guard.h)
+    std::vector<cbessfm_batch::Group> groups;
     std::vector<int2> items;
     for (const auto& kv : by_shape) {
         cbessfm_batch::Group gr;
@@ -117,10 +114,8 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
             gr.tbl_bytes = tw;
             gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb, gr.tbl_bytes);
         }
-        if (gr.G < 1) {
-            free_batch(b);
+        if (gr.G < 1)
             return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape for n_fft %d, bands %d", gr.np, gr.n_sb);
-        }
         gr.threads = gr.G * tb;
         // work items: G consecutive blocks of one job, longest processing time first
         std::vector<std::pair<int, int2>> its;
@@ -142,13 +137,16 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
         int per_sm = 0;
         e = forward_persistent_occupancy(gr.np, gr.storage, gr.threads,
                                          gr.G * gr.region_bytes + gr.tbl_bytes, &per_sm);
-        if (e != cudaSuccess || per_sm < 1) {
-            free_batch(b);
+        if (e != cudaSuccess || per_sm < 1)
             return e != cudaSuccess ? cuda_fail(e, "occupancy") : fail(CBESSFM_ERR_UNSUPPORTED, "persistent kernel does not fit an SM");
-        }
         gr.grid = (int)std::min<long long>((long long)per_sm * n_sm, gr.n_items);
-        b->groups.push_back(gr);
+        groups.push_back(gr);
     }
+
+    cbessfm_batch* b = new (std::nothrow) cbessfm_batch;
+    if (b == nullptr) return fail(CBESSFM_ERR_OOM, "host allocation of the batch failed");
+    b->njobs = njobs;
+    b->groups.swap(groups);
     b->total_items = (long long)items.size();
 
     e = cudaMalloc(&b->d_jobs, sizeof(ChainArgs) * args.size());
@@ -164,6 +162,11 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
     }
     *out = b;
     return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_batch** out) {
+    clear_error();
+    return abi_guard([&] { return batch_create_body(jobs, njobs, out); });
 }
 
 cbessfm_status cbessfm_batch_run(const cbessfm_batch* b, cbessfm_stream stream) {

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <vector>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace cbessfm {
@@ -102,10 +103,9 @@ using namespace cbessfm;
 
 extern "C" {
 
-cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int steps,
-                                     int spans_per_step, const double* step_power, int ntaps,
-                                     int grid, double* taps, double* response) {
-    clear_error();
+static cbessfm_status analytic_taps_body(const cbessfm_link* link, int bands, int steps,
+                                         int spans_per_step, const double* step_power, int ntaps,
+                                         int grid, double* taps, double* response) {
     if (link == nullptr || taps == nullptr || (steps > 0 && step_power == nullptr))
         return fail(CBESSFM_ERR_INVALID_ARG, "link, taps or step_power is NULL");
     if (bands < 1 || bands > 16) return fail(CBESSFM_ERR_INVALID_ARG, "bands must be in [1, 16]");
@@ -126,13 +126,13 @@ cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int st
                     steps, spans_per_step, link->n_spans);
     const int n_sep = 2 * bands - 1;
     const int n_out = n_sep * ntaps;
+    std::vector<double2> c(n_out);                 // before the device allocation (abi_guard.h)
     double2* d_out = nullptr;
     cudaError_t e = cudaMalloc(&d_out, sizeof(double2) * n_out);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(coefficients)");
     coeff_kernel<<<n_out, kCoeffThreads>>>(d_out, bands, ntaps, grid, link->sample_rate / bands,
                                            link->beta2, link->gamma, link->alpha, L, spans_per_step);
     e = cudaGetLastError();
-    std::vector<double2> c(n_out);
     if (e == cudaSuccess) e = cudaMemcpy(c.data(), d_out, sizeof(double2) * n_out, cudaMemcpyDeviceToHost);
     cudaFree(d_out);
     if (e != cudaSuccess) return cuda_fail(e, "analytic coefficients");
@@ -150,6 +150,16 @@ cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int st
             response[2 * k + 1] = c[k].y;
         }
     return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int steps,
+                                     int spans_per_step, const double* step_power, int ntaps,
+                                     int grid, double* taps, double* response) {
+    clear_error();
+    return abi_guard([&] {
+        return analytic_taps_body(link, bands, steps, spans_per_step, step_power, ntaps, grid,
+                                  taps, response);
+    });
 }
 
 }  // extern "C"

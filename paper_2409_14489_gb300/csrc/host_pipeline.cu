@@ -17,6 +17,7 @@
 #include <mutex>
 #include <new>
 
+#include "abi_guard.h"
 #include "internal.h"
 
 namespace cbessfm {
@@ -67,10 +68,10 @@ using namespace cbessfm;
 
 extern "C" {
 
-cbessfm_status cbessfm_backpropagate_host(cbessfm_plan* plan, const void* host_in, void* host_out,
-                                          void* dev_in, void* dev_out, int64_t n_samples,
-                                          int batch, int launch_blocks, cbessfm_stream stream) {
-    clear_error();
+static cbessfm_status backpropagate_host_body(cbessfm_plan* plan, const void* host_in,
+                                              void* host_out, void* dev_in, void* dev_out,
+                                              int64_t n_samples, int batch, int launch_blocks,
+                                              cbessfm_stream stream) {
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     if (!host_in || !host_out || !dev_in || !dev_out)
         return fail(CBESSFM_ERR_INVALID_ARG, "host_in/host_out/dev_in/dev_out is NULL");
@@ -183,6 +184,17 @@ cbessfm_status cbessfm_backpropagate_host(cbessfm_plan* plan, const void* host_i
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, hp.end, 0);   // completion on `stream`
     if (e != cudaSuccess) return cuda_fail(e, "pipeline end");
     return CBESSFM_OK;
+}
+
+cbessfm_status cbessfm_backpropagate_host(cbessfm_plan* plan, const void* host_in, void* host_out,
+                                          void* dev_in, void* dev_out, int64_t n_samples,
+                                          int batch, int launch_blocks, cbessfm_stream stream) {
+    clear_error();
+    // the pipeline's mutexes are the one thing here that can throw
+    return abi_guard([&] {
+        return backpropagate_host_body(plan, host_in, host_out, dev_in, dev_out, n_samples, batch,
+                                       launch_blocks, stream);
+    });
 }
 
 }  // extern "C"

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "abi_guard.h"
 #include "fwd_kernel.cuh"
 #include "internal.h"
 
@@ -255,7 +256,8 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
     if (dev < 0 || dev >= kMaxDevices) return fail(CBESSFM_ERR_UNSUPPORTED, "device index %d", dev);
     unsigned char* scratch = nullptr;
     int n_sm = 0;
-    const cbessfm_status st0 = device_setup(dev, &scratch, &n_sm);
+    // the set-up's mutex is the one thing here that can throw
+    const cbessfm_status st0 = abi_guard([&] { return device_setup(dev, &scratch, &n_sm); });
     if (st0 != CBESSFM_OK) return st0;
     int per_sm = 0;
     e = noalloc_occupancy(np, G * tb, G * region + tbl, &per_sm);

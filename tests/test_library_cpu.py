@@ -160,3 +160,31 @@ def test_plan_and_batch_close_idempotently_as_context_managers(lib):
         assert not obj._h.value
         obj.close()
         obj.__del__()
+
+
+_GUARD_CHILD = r"""
+import ctypes, resource, sys
+so = ctypes.CDLL(sys.argv[1])
+so.cbessfm_last_error.restype = ctypes.c_char_p
+job = ctypes.create_string_buffer(64)                 # one zeroed job; never read (see below)
+out = ctypes.c_void_p()
+vm = int([l.split()[1] for l in open("/proc/self/status") if l.startswith("VmSize")][0]) * 1024
+resource.setrlimit(resource.RLIMIT_AS, (vm + (256 << 20), resource.RLIM_INFINITY))
+st = so.cbessfm_batch_create(job, (1 << 31) - 1, ctypes.byref(out))
+print(st, so.cbessfm_last_error().decode(), out.value)
+"""
+
+
+def test_host_allocation_failure_is_a_status_not_an_exception(lib):
+    """No C++ exception crosses the ABI: under an address-space limit, batch_create's first host
+    container (one descriptor per job, here 2^31 - 1 of them, allocated before any job is read)
+    cannot be allocated, and the call returns CBESSFM_ERR_OOM with a message and no batch instead
+    of terminating the process.  Run in a child process, which the limit confines."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", _GUARD_CHILD, lib._LIB_PATH],
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr[-2000:]
+    st, rest = r.stdout.strip().split(" ", 1)
+    assert int(st) == lib.ERR_OOM, r.stdout
+    assert "host resources exhausted" in rest and rest.endswith("None"), r.stdout
