@@ -254,24 +254,28 @@ class Plan:
         import torch
         if not (grad_out.is_cuda and grad_out.dtype == torch.complex64):
             raise ValueError("grad_out must be a complex64 CUDA tensor")
-        g = grad_out.contiguous()
-        batch, L = self._shape(g)
-        gc = torch.zeros((max(self.steps, 0), self.bands, self.bands, self.ntaps),
-                         dtype=torch.float64, device="cuda")
-        gr = torch.zeros((), dtype=torch.float64, device="cuda") if want_ratio else None
-        gi = torch.empty_like(g) if want_input else None
-        _check(_lib.cbessfm_grad(self._h, g.data_ptr(), gc.data_ptr() if gc.numel() else None,
-                                 gr.data_ptr() if gr is not None else None,
-                                 gi.data_ptr() if gi is not None else None,
-                                 workspace.data_ptr(), workspace.numel(), L, batch,
-                                 _stream_handle(stream)))
+        # temporaries and outputs are made on the call's stream, so their fills and their
+        # memory's reuse are ordered with the kernels (a no-op without an explicit stream)
+        with torch.cuda.stream(stream):
+            g = grad_out.contiguous()
+            batch, L = self._shape(g)
+            gc = torch.zeros((max(self.steps, 0), self.bands, self.bands, self.ntaps),
+                             dtype=torch.float64, device="cuda")
+            gr = torch.zeros((), dtype=torch.float64, device="cuda") if want_ratio else None
+            gi = torch.empty_like(g) if want_input else None
+            _check(_lib.cbessfm_grad(self._h, g.data_ptr(), gc.data_ptr() if gc.numel() else None,
+                                     gr.data_ptr() if gr is not None else None,
+                                     gi.data_ptr() if gi is not None else None,
+                                     workspace.data_ptr(), workspace.numel(), L, batch,
+                                     _stream_handle(stream)))
         return gc, gr, gi
 
     def set_coeffs(self, coeffs, stream=None):
         import torch
         if isinstance(coeffs, torch.Tensor) and coeffs.is_cuda:
-            c = coeffs.detach().to(torch.float32).contiguous()
-            _check(_lib.cbessfm_set_coeffs(self._h, c.data_ptr(), 1, _stream_handle(stream)))
+            with torch.cuda.stream(stream):   # a converted copy is freed in order with the copy
+                c = coeffs.detach().to(torch.float32).contiguous()
+                _check(_lib.cbessfm_set_coeffs(self._h, c.data_ptr(), 1, _stream_handle(stream)))
             return c
         c = np.ascontiguousarray(np.asarray(coeffs, dtype=np.float32))
         _check(_lib.cbessfm_set_coeffs(self._h, c.ctypes.data, 0, _stream_handle(stream)))
@@ -303,15 +307,17 @@ class Plan:
         """Per-step streamed form (``cbessfm_backpropagate_streamed``); complex64 only."""
         import torch
         batch, L = self._shape(x)
-        if out is None:
-            out = torch.empty_like(x)
         need = self.streamed_workspace_size(L, batch)
-        if workspace is None and need:
-            workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
-        _check(_lib.cbessfm_backpropagate_streamed(
-            self._h, x.data_ptr(), out.data_ptr(),
-            workspace.data_ptr() if workspace is not None else None,
-            workspace.numel() if workspace is not None else 0, L, batch, _stream_handle(stream)))
+        with torch.cuda.stream(stream):       # a workspace made here is freed in order with the passes
+            if out is None:
+                out = torch.empty_like(x)
+            if workspace is None and need:
+                workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
+            _check(_lib.cbessfm_backpropagate_streamed(
+                self._h, x.data_ptr(), out.data_ptr(),
+                workspace.data_ptr() if workspace is not None else None,
+                workspace.numel() if workspace is not None else 0, L, batch,
+                _stream_handle(stream)))
         return out
 
     def set_nlpr_mode(self, per_polarization: bool):
