@@ -361,12 +361,19 @@ class Batch:
     of jobs sharing N', subband count and storage.  ``run()`` is graph-capturable."""
 
     def __init__(self, jobs):
+        self._h = ctypes.c_void_p()
         self._jobs = list(jobs)            # keep plans and tensors alive
         arr = (JobStruct * len(self._jobs))()
         for k, (plan, x, y) in enumerate(self._jobs):
-            n = x.shape[-2] if x.dim() >= 2 else x.shape[0]
-            arr[k] = JobStruct(plan.handle.value, x.data_ptr(), y.data_ptr(), int(n))
-        self._h = ctypes.c_void_p()
+            # one realization per job: a (batch, L, ...) field would be cut to its first row
+            want = plan._field_dtype()
+            last = 2 if plan.storage == STORAGE_C64 else 4
+            for name, t in (("x", x), ("y", y)):
+                if not (t.is_cuda and t.dtype == want and t.is_contiguous() and t.dim() == 2
+                        and t.shape[1] == last and t.shape == x.shape):
+                    raise ValueError(f"job {k}: {name} must be a contiguous {want} CUDA tensor "
+                                     f"of shape (L, {last}), the same for x and y")
+            arr[k] = JobStruct(plan.handle.value, x.data_ptr(), y.data_ptr(), int(x.shape[0]))
         _check(_lib.cbessfm_batch_create(arr, len(self._jobs), ctypes.byref(self._h)))
 
     def run(self, stream=None):

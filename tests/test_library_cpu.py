@@ -188,3 +188,17 @@ def test_host_allocation_failure_is_a_status_not_an_exception(lib):
     st, rest = r.stdout.strip().split(" ", 1)
     assert int(st) == lib.ERR_OOM, r.stdout
     assert "host resources exhausted" in rest and rest.endswith("None"), r.stdout
+
+
+def test_batch_jobs_are_validated_before_the_library_call(lib):
+    """A job's x and y must be (L, 2) complex64 (or (L, 4) 16-bit) CUDA tensors of equal shape:
+    host tensors, or a (batch, L, 2) field that a job would cut to its first realization, are
+    refused with ValueError before cbessfm_batch_create runs."""
+    import torch
+    plan = object.__new__(lib.Plan)
+    plan._h = ctypes.c_void_p()
+    plan.storage = lib.STORAGE_C64
+    x = torch.zeros((64, 2), dtype=torch.complex64)
+    for bad in [(x, x), (x.reshape(1, 64, 2), x.reshape(1, 64, 2))]:
+        with pytest.raises(ValueError, match="job 0: x must be a contiguous"):
+            lib.Batch([(plan, *bad)])
