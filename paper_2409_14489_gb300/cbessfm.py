@@ -190,25 +190,33 @@ class Plan:
         return {STORAGE_C64: torch.complex64, STORAGE_F16X4: torch.float16,
                 STORAGE_BF16X4: torch.bfloat16}[self.storage]
 
+    def _field(self, t, name: str, like=None, c64: bool = False, host: bool = False):
+        """(batch, L) of a contiguous field in the plan's storage (complex64 when ``c64``) of
+        shape (L, k) or (batch, L, k), k = 2 for complex64 and 4 for 16-bit storage, on the
+        device (in host memory when ``host``); ``like`` is a field it must match in shape.  The
+        library reads and writes whole samples from these shapes, so a wrong one is refused here."""
+        import torch
+        want = torch.complex64 if c64 else self._field_dtype()
+        last = 2 if want == torch.complex64 else 4
+        ok = (isinstance(t, torch.Tensor) and t.is_cuda != host and t.dtype == want
+              and t.is_contiguous() and t.dim() in (2, 3) and t.shape[-1] == last
+              and (like is None or t.shape == like.shape))
+        if not ok:
+            where = "host" if host else "CUDA"
+            raise ValueError(f"{name} must be a contiguous {want} {where} tensor of shape "
+                             f"(L, {last}) or (batch, L, {last})"
+                             + ("" if like is None else ", the same as x"))
+        return self._shape(t)
+
     def backpropagate(self, x, out=None, stream=None):
         """Run DBP on a contiguous CUDA tensor in the plan's storage: complex64 of shape (L, 2) or
         (batch, L, 2); for fp16/bf16 storage, float16/bfloat16 of shape (L, 4) or (batch, L, 4)
         holding (x.re, x.im, y.re, y.im)."""
         import torch
-        want = self._field_dtype()
-        last = 2 if self.storage == STORAGE_C64 else 4
-        if not (x.is_cuda and x.dtype == want and x.is_contiguous()):
-            raise ValueError(f"x must be a contiguous {want} CUDA tensor")
-        if x.dim() == 2:
-            batch, L = 1, x.shape[0]
-        elif x.dim() == 3:
-            batch, L = x.shape[0], x.shape[1]
-        else:
-            raise ValueError(f"x must have shape (L, {last}) or (batch, L, {last})")
-        if x.shape[-1] != last:
-            raise ValueError(f"last dimension must be {last}")
+        batch, L = self._field(x, "x")
         if out is None:
             out = torch.empty_like(x)
+        self._field(out, "out", like=x)
         _check(_lib.cbessfm_backpropagate(self._h, x.data_ptr(), out.data_ptr(), L, batch,
                                           _stream_handle(stream)))
         return out
@@ -236,11 +244,10 @@ class Plan:
     def backpropagate_checkpointed(self, x, workspace, out=None, stream=None):
         """Forward chain that also stores the adjoint's checkpoints in ``workspace``."""
         import torch
-        if not (x.is_cuda and x.dtype == torch.complex64 and x.is_contiguous()):
-            raise ValueError("x must be a contiguous complex64 CUDA tensor")
-        batch, L = self._shape(x)
+        batch, L = self._field(x, "x")          # the library refuses 16-bit storage here
         if out is None:
             out = torch.empty_like(x)
+        self._field(out, "out", like=x)
         _check(_lib.cbessfm_backpropagate_checkpointed(
             self._h, x.data_ptr(), out.data_ptr(), L, batch, workspace.data_ptr(),
             workspace.numel(), _stream_handle(stream)))
@@ -252,13 +259,14 @@ class Plan:
         ntaps] float64, dL/dratio float64 scalar or None, dL/din complex64 or None).  Leaving
         out the ratio gradient skips its per-step work in the adjoint kernel."""
         import torch
-        if not (grad_out.is_cuda and grad_out.dtype == torch.complex64):
+        if not (isinstance(grad_out, torch.Tensor) and grad_out.is_cuda
+                and grad_out.dtype == torch.complex64):
             raise ValueError("grad_out must be a complex64 CUDA tensor")
         # temporaries and outputs are made on the call's stream, so their fills and their
         # memory's reuse are ordered with the kernels (a no-op without an explicit stream)
         with torch.cuda.stream(stream):
             g = grad_out.contiguous()
-            batch, L = self._shape(g)
+            batch, L = self._field(g, "grad_out", c64=True)
             gc = torch.zeros((max(self.steps, 0), self.bands, self.bands, self.ntaps),
                              dtype=torch.float64, device="cuda")
             gr = torch.zeros((), dtype=torch.float64, device="cuda") if want_ratio else None
@@ -286,13 +294,10 @@ class Plan:
         ``h_in``/``h_out`` pinned CPU tensors, ``d_in``/``d_out`` CUDA tensors of the same shape;
         ``launch_blocks`` OLS blocks per kernel launch (0: one wave of the device).  Completion is
         ordered on ``stream`` (the current stream by default)."""
-        for t in (h_in, h_out):
-            if t.is_cuda or not t.is_contiguous():
-                raise ValueError("h_in/h_out must be contiguous host tensors")
-        for t in (d_in, d_out):
-            if not t.is_cuda or not t.is_contiguous():
-                raise ValueError("d_in/d_out must be contiguous CUDA tensors")
-        batch, L = self._shape(h_in)
+        batch, L = self._field(h_in, "h_in", host=True)
+        self._field(h_out, "h_out", like=h_in, host=True)
+        self._field(d_in, "d_in", like=h_in)
+        self._field(d_out, "d_out", like=h_in)
         _check(_lib.cbessfm_backpropagate_host(self._h, h_in.data_ptr(), h_out.data_ptr(),
                                                d_in.data_ptr(), d_out.data_ptr(), L, batch,
                                                launch_blocks, _stream_handle(stream)))
@@ -306,7 +311,9 @@ class Plan:
     def backpropagate_streamed(self, x, out=None, workspace=None, stream=None):
         """Per-step streamed form (``cbessfm_backpropagate_streamed``); complex64 only."""
         import torch
-        batch, L = self._shape(x)
+        batch, L = self._field(x, "x")          # the library refuses 16-bit storage here
+        if out is not None:
+            self._field(out, "out", like=x)
         need = self.streamed_workspace_size(L, batch)
         with torch.cuda.stream(stream):       # a workspace made here is freed in order with the passes
             if out is None:

@@ -202,3 +202,38 @@ def test_batch_jobs_are_validated_before_the_library_call(lib):
     for bad in [(x, x), (x.reshape(1, 64, 2), x.reshape(1, 64, 2))]:
         with pytest.raises(ValueError, match="job 0: x must be a contiguous"):
             lib.Batch([(plan, *bad)])
+
+
+def test_field_checks_of_the_binding(lib):
+    """The binding refuses fields whose size the library would misread: wrong dtype for the
+    plan's storage, a last dimension other than 2 (complex64) or 4 (16-bit), another rank, a
+    non-contiguous view, an output of another shape, or host/device memory in the wrong place."""
+    import torch
+    plan = object.__new__(lib.Plan)
+    plan._h = ctypes.c_void_p()
+    plan.storage = lib.STORAGE_C64
+    x = torch.zeros((3, 40, 2), dtype=torch.complex64)
+    assert plan._field(x, "x", host=True) == (3, 40)
+    assert plan._field(x[0], "x", host=True) == (1, 40)
+    assert plan._field(x, "out", like=x, host=True) == (3, 40)
+    bad = [x.to(torch.complex128), x.reshape(3, 80, 1), x.reshape(240), x[:, ::2],
+           torch.zeros((3, 40, 4), dtype=torch.float16)]
+    for t in bad:
+        with pytest.raises(ValueError, match="x must be a contiguous"):
+            plan._field(t, "x", host=True)
+    with pytest.raises(ValueError, match="the same as x"):
+        plan._field(x[:2], "out", like=x, host=True)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        plan._field(x, "x")
+    plan.storage = lib.STORAGE_F16X4
+    assert plan._field(torch.zeros((40, 4), dtype=torch.float16), "x", host=True) == (1, 40)
+    with pytest.raises(ValueError, match="float16"):
+        plan._field(x, "x", host=True)
+    # the public calls check before any library call
+    with pytest.raises(ValueError, match="h_in must be a contiguous torch.float16 host tensor"):
+        plan.backpropagate_host(x, x, x, x)
+    plan.storage = lib.STORAGE_C64
+    with pytest.raises(ValueError, match="d_in must be a contiguous torch.complex64 CUDA"):
+        plan.backpropagate_host(x, x, x, x)
+    with pytest.raises(ValueError, match="x must be a contiguous torch.complex64 CUDA"):
+        plan.backpropagate(x)
