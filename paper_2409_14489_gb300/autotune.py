@@ -52,19 +52,23 @@ def overlap_for(shape: JobShape) -> int:
     return max(16, int(math.ceil(per_sb / 16.0)) * 16)
 
 
+def _block_fits(n_fft: int, n_sb: int) -> bool:
+    """Whether the chain kernel takes N' = n_fft with n_sb subbands in one CTA (threads and
+    shared memory per block)."""
+    return not (n_fft == 2048 and n_sb > 5) and not (n_fft == 1024 and n_sb > 10)
+
+
 def candidates(shape: JobShape):
     ov = overlap_for(shape)
-    out = []
-    for nf in CANDIDATE_NFFT:
-        if nf <= ov or shape.ntaps > nf // 2:
-            continue
-        if nf == 2048 and shape.n_sb > 5:
-            continue
-        if nf == 1024 and shape.n_sb > 10:
-            continue
-        out.append((nf, ov))
-    if not out:                     # memory longer than any block: largest block, capped overlap
-        out.append((2048, min(ov, 1536)))
+    fitting = [nf for nf in CANDIDATE_NFFT
+               if _block_fits(nf, shape.n_sb) and shape.ntaps <= nf // 2]
+    if not fitting:
+        raise ValueError(f"no block size takes {shape.ntaps} taps with {shape.n_sb} subbands")
+    out = [(nf, ov) for nf in fitting if nf > ov]
+    if not out:
+        # memory longer than any block: the largest block that fits, overlap capped at 3/4 of it
+        nf = fitting[-1]
+        out.append((nf, min(ov, 3 * nf // 4)))
     return out
 
 
@@ -76,7 +80,8 @@ def model_cost(shape: JobShape, n_fft: int, overlap: int) -> float:
 
 class Autotuner:
     def __init__(self, mode: str = "measure", cache_path: Optional[str] = None):
-        assert mode in ("measure", "model")
+        if mode not in ("measure", "model"):
+            raise ValueError(f"mode must be 'measure' or 'model', not {mode!r}")
         self.mode = mode
         self.cache_path = cache_path or os.environ.get(
             "CBESSFM_AUTOTUNE_CACHE", os.path.join(_HERE, "_build", "autotune.json"))

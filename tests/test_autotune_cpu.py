@@ -36,8 +36,14 @@ def test_candidates_respect_overlap_taps_and_block_limits():
     assert all(ov == 672 for _, ov in autotune.candidates(s))
     assert [nf for nf, _ in autotune.candidates(_shape(ntaps=601))] == [2048]
     assert 2048 not in [nf for nf, _ in autotune.candidates(_shape(n_sb=6))]
-    # memory longer than any block: the largest block with a capped overlap
+    # memory longer than any block: the largest block that fits, overlap capped at 3/4 of it
     assert autotune.candidates(_shape(L=5000e3)) == [(2048, 1536)]
+    assert autotune.candidates(_shape(n_sb=6, L=50000e3)) == [(1024, 768)]
+    assert autotune.candidates(_shape(n_sb=12, L=50000e3)) == [(512, 384)]
+    with pytest.raises(ValueError, match="taps"):
+        autotune.candidates(_shape(ntaps=1025))
+    with pytest.raises(ValueError, match="mode"):
+        autotune.Autotuner("fastest")
 
 
 def test_model_mode_picks_the_cheapest_candidate():
