@@ -113,8 +113,14 @@ cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_strea
  *   in, out    device arrays [batch][n_samples] 4D samples in the plan's storage type; out
  *              must not overlap in (ALIAS).
  *   n_samples  L >= 1 samples per sequence (one period); any length, blocks wrap circularly.
- * One kernel launch: each CTA stages its overlap-and-save blocks into shared memory with the
- * Tensor Memory Accelerator and runs the whole chain on chip.
+ * One kernel launch: each CTA stages its overlap-and-save blocks into shared memory and runs
+ * the whole chain on chip.  Staging uses bulk copies of the Tensor Memory Accelerator, except
+ * that 16-bit samples use coalesced loads where a copy would not start on a 16-byte boundary
+ * (odd L or an odd block start).
+ * Errors: INVALID_ARG for a NULL plan or buffer, in/out not 16-byte aligned, or n_samples or
+ * batch < 1; ALIAS when out overlaps in; UNSUPPORTED beyond 2^31 - 1 blocks in one call; CUDA
+ * when the launch fails.  A bounded in-kernel wait that gives up is reported later by
+ * cbessfm_get_status.
  */
 cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, void* out,
                                      int64_t n_samples, int batch, cbessfm_stream stream);
