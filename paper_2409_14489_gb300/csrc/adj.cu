@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "block_count.h"
 #include "fwd_kernel.cuh"
 #include "internal.h"
 
@@ -596,9 +597,11 @@ struct Layout {
     int part_stride;
 };
 
+// callers first refuse calls of more than 2^31 - 1 blocks (too_many_blocks), which bounds every
+// size below
 Layout layout(const PlanImpl& p, long long n_samples, int batch) {
     Layout l{};
-    const long long nb = (n_samples + p.V - 1) / p.V;
+    const long long nb = blocks_for(n_samples, p.V);
     l.n_blk = nb * batch;
     l.ckpt_bytes = (size_t)l.n_blk * (size_t)(p.n_st + 2) * 16 * p.N;
     l.stash_bytes = p.n_st > 0 ? (size_t)l.n_blk * 2 * 16 * p.N : 0;
@@ -621,13 +624,14 @@ cbessfm_status check_common(const cbessfm_plan* plan, int64_t n_samples, int bat
     if (p->per_pol)
         return fail(CBESSFM_ERR_UNSUPPORTED, "gradients cover the Manakov NLPR only");
     if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
+    if (too_many_blocks(blocks_for(n_samples, p->V), batch))
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks");
     if (workspace == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(workspace) & 255u)
         return fail(CBESSFM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     const Layout l = layout(*p, n_samples, batch);
     if (ws_bytes < l.total)
         return fail(CBESSFM_ERR_INVALID_ARG, "workspace of %zu bytes is smaller than %zu", ws_bytes, l.total);
-    if (l.n_blk > (1ll << 31) - 1) return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks");
     if (adj_region_bytes(*p) + chain_tw_bytes(fft_tw_size(p->n_fft)) > kMaxDynSmem)
         return fail(CBESSFM_ERR_UNSUPPORTED, "the adjoint of a %d-sample block does not fit shared memory",
                     p->N);
@@ -648,6 +652,8 @@ cbessfm_status cbessfm_grad_workspace_size(const cbessfm_plan* plan, int64_t n_s
     const PlanImpl* p = plan_impl(plan);
     if (p == nullptr || bytes == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan/bytes is NULL");
     if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
+    if (too_many_blocks(blocks_for(n_samples, p->V), batch))
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks");
     *bytes = layout(*p, n_samples, batch).total;
     return CBESSFM_OK;
 }
@@ -670,7 +676,7 @@ cbessfm_status cbessfm_backpropagate_checkpointed(const cbessfm_plan* plan, cons
     a.out = out;
     a.L = n_samples;
     a.batch = batch;
-    a.n_blocks = (int)((n_samples + p->V - 1) / p->V);
+    a.n_blocks = (int)blocks_for(n_samples, p->V);
     a.ckpt = static_cast<float2*>(workspace);
     const cudaError_t e = dispatch<false>(p->n_fft, a, p->threads, reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward launch");
@@ -695,7 +701,7 @@ cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, doub
     ChainArgs a = make_chain_args(*p);
     a.L = n_samples;
     a.batch = batch;
-    a.n_blocks = (int)((n_samples + p->V - 1) / p->V);
+    a.n_blocks = (int)blocks_for(n_samples, p->V);
     a.ckpt = reinterpret_cast<float2*>(ws);
     a.stash = reinterpret_cast<float2*>(ws + l.ckpt_bytes);
     a.gpart = reinterpret_cast<float*>(ws + l.ckpt_bytes + l.stash_bytes);

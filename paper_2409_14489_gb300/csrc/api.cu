@@ -12,6 +12,7 @@
 
 #include "device_common.cuh"
 #include "abi_guard.h"
+#include "block_count.h"
 #include "internal.h"
 
 
@@ -228,12 +229,12 @@ cbessfm_status forward_range(const cbessfm_plan* plan, const void* in, void* out
     const unsigned long long sample_bytes = p.storage == CBESSFM_C64 ? 16ull : 8ull;
     if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u)
         return fail(CBESSFM_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
+    const long long n_blocks = blocks_for(n_samples, p.V);
+    if (too_many_blocks(n_blocks, batch))
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
     const unsigned long long bytes = (unsigned long long)n_samples * batch * sample_bytes;
     const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
     if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
-    const long long n_blocks = (n_samples + p.V - 1) / p.V;
-    if (n_blocks * batch > (1ll << 31) - 1)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
     const long long ctas = (n_blocks * batch + p.G - 1) / p.G;
     if (cta0 < 0 || n_ctas < 0 || cta0 > ctas)
         return fail(CBESSFM_ERR_INVALID_ARG, "CTA range %d + %d outside the batch's %lld", cta0,
@@ -481,6 +482,8 @@ cbessfm_status cbessfm_streamed_workspace_size(const cbessfm_plan* plan, int64_t
     clear_error();
     if (plan == nullptr || bytes == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan/bytes is NULL");
     if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
+    if (too_many_blocks(blocks_for(n_samples, plan->impl.V), batch))
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
     const size_t one = ((size_t)n_samples * batch * 16 + 255) / 256 * 256;
     *bytes = streamed_buffers(plan->impl) * one;
     return CBESSFM_OK;
@@ -497,6 +500,9 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
     if (p.n_st <= 1) return cbessfm_backpropagate(plan, in, out, n_samples, batch, stream);
     if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
     if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
+    const long long n_blocks = blocks_for(n_samples, p.V);
+    if (too_many_blocks(n_blocks, batch))
+        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
     const size_t one = ((size_t)n_samples * batch * 16 + 255) / 256 * 256;
     if (workspace == nullptr || ws_bytes < streamed_buffers(p) * one)
         return fail(CBESSFM_ERR_INVALID_ARG, "workspace of %zu bytes is smaller than %zu", ws_bytes,
@@ -510,9 +516,6 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
     if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
     if ((i0 < w1 && w0 < i0 + bytes) || (o0 < w1 && w0 < o0 + bytes))
         return fail(CBESSFM_ERR_ALIAS, "workspace overlaps in or out");
-    const long long n_blocks = (n_samples + p.V - 1) / p.V;
-    if (n_blocks * batch > (1ll << 31) - 1)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
     unsigned char* buf[2] = {static_cast<unsigned char*>(workspace),
                              static_cast<unsigned char*>(workspace) + one};
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

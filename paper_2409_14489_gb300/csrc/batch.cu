@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "abi_guard.h"
+#include "block_count.h"
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -67,12 +68,12 @@ static cbessfm_status batch_create_body(const cbessfm_job* jobs, int njobs, cbes
         if (jb.n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "job %d: n_samples < 1", k);
         if ((reinterpret_cast<uintptr_t>(jb.in) | reinterpret_cast<uintptr_t>(jb.out)) & 15u)
             return fail(CBESSFM_ERR_INVALID_ARG, "job %d: in/out must be 16-byte aligned", k);
+        const long long nb = blocks_for(jb.n_samples, p->V);
+        if (nb > (1ll << 30)) return fail(CBESSFM_ERR_UNSUPPORTED, "job %d: too many blocks", k);
         const unsigned long long sb = p->storage == CBESSFM_C64 ? 16ull : 8ull;
         const unsigned long long bytes = (unsigned long long)jb.n_samples * sb;
         const uintptr_t i0 = reinterpret_cast<uintptr_t>(jb.in), o0 = reinterpret_cast<uintptr_t>(jb.out);
         if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "job %d: out overlaps in", k);
-        const long long nb = (jb.n_samples + p->V - 1) / p->V;
-        if (nb > (1ll << 30)) return fail(CBESSFM_ERR_UNSUPPORTED, "job %d: too many blocks", k);
         ChainArgs a = make_chain_args(*p);
         a.in = jb.in;
         a.out = jb.out;

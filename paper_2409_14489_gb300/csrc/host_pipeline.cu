@@ -18,6 +18,7 @@
 #include <new>
 
 #include "abi_guard.h"
+#include "block_count.h"
 #include "internal.h"
 
 namespace cbessfm {
@@ -82,8 +83,8 @@ static cbessfm_status backpropagate_host_body(cbessfm_plan* plan, const void* ho
     const size_t per_seq = (size_t)n_samples * sample_bytes;
     if ((per_seq & 15) && batch > 1)
         return fail(CBESSFM_ERR_INVALID_ARG, "each realization must span a multiple of 16 bytes");
-    const long long n_blocks = (n_samples + p.V - 1) / p.V;
-    if (n_blocks * batch > (1ll << 31) - 1)
+    const long long n_blocks = blocks_for(n_samples, p.V);
+    if (too_many_blocks(n_blocks, batch))
         return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks in one call");
     const int total = (int)(n_blocks * batch);
     const uintptr_t di = reinterpret_cast<uintptr_t>(dev_in), dO = reinterpret_cast<uintptr_t>(dev_out);

@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "abi_guard.h"
+#include "block_count.h"
 #include "fwd_kernel.cuh"
 #include "internal.h"
 
@@ -200,11 +201,11 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
         }
         if (p->per_pol)
             return fail(CBESSFM_ERR_UNSUPPORTED, "job %d: the per-polarization NLPR is not supported here", k);
+        const long long nb = blocks_for(jb.n_samples, p->V);
+        if (nb > (1ll << 30)) return fail(CBESSFM_ERR_UNSUPPORTED, "job %d: too many blocks", k);
         const unsigned long long bytes = (unsigned long long)jb.n_samples * 16ull;
         const uintptr_t i0 = reinterpret_cast<uintptr_t>(jb.in), o0 = reinterpret_cast<uintptr_t>(jb.out);
         if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "job %d: out overlaps in", k);
-        const long long nb = (jb.n_samples + p->V - 1) / p->V;
-        if (nb > (1ll << 30)) return fail(CBESSFM_ERR_UNSUPPORTED, "job %d: too many blocks", k);
         desc[k] = make_chain_args(*p);
         desc[k].in = jb.in;
         desc[k].out = jb.out;

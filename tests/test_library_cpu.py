@@ -237,3 +237,16 @@ def test_field_checks_of_the_binding(lib):
         plan.backpropagate_host(x, x, x, x)
     with pytest.raises(ValueError, match="x must be a contiguous torch.complex64 CUDA"):
         plan.backpropagate(x)
+
+
+def test_block_count_helpers_do_not_overflow(tmp_path):
+    """Every entry point refuses more than 2^31 - 1 blocks before it forms a size from
+    n_samples * batch; the helpers it uses are exact at the int64 and int32 limits."""
+    import subprocess
+    src = os.path.join(ROOT, "tests", "block_count_check.cc")
+    inc = os.path.join(ROOT, "paper_2409_14489_gb300", "csrc")
+    exe = str(tmp_path / "block_count_check")
+    subprocess.run(["g++", "-std=c++17", "-O2", "-Wall", "-Werror", "-I", inc, src, "-o", exe],
+                   check=True, capture_output=True, text=True, timeout=120)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stdout
