@@ -279,7 +279,12 @@ class Plan:
         return gc, gr, gi
 
     def set_coeffs(self, coeffs, stream=None):
+        """Replace the taps: ``[steps][bands][bands][ntaps]`` as at creation, a host array (the
+        copy is synchronous) or a CUDA tensor (copied on ``stream``)."""
         import torch
+        want = (self.steps, self.bands, self.bands, self.ntaps)
+        if self.steps > 0 and tuple(coeffs.shape) != want:
+            raise ValueError(f"coeffs must have shape {want}, not {tuple(coeffs.shape)}")
         if isinstance(coeffs, torch.Tensor) and coeffs.is_cuda:
             with torch.cuda.stream(stream):   # a converted copy is freed in order with the copy
                 c = coeffs.detach().to(torch.float32).contiguous()

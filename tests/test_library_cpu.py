@@ -250,3 +250,15 @@ def test_block_count_helpers_do_not_overflow(tmp_path):
                    check=True, capture_output=True, text=True, timeout=120)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stdout
+
+
+def test_set_coeffs_checks_the_tap_shape(lib):
+    """set_coeffs refuses taps of another shape than the plan's [steps][bands][bands][ntaps]
+    before the library reads them (it would read past a shorter array)."""
+    import numpy as np
+    plan = object.__new__(lib.Plan)
+    plan._h = ctypes.c_void_p()
+    plan.steps, plan.bands, plan.ntaps = 2, 3, 5
+    for shape in [(2, 3, 3, 3), (1, 3, 3, 5), (90,)]:
+        with pytest.raises(ValueError, match=r"coeffs must have shape \(2, 3, 3, 5\)"):
+            plan.set_coeffs(np.zeros(shape, np.float32))
