@@ -238,6 +238,16 @@ class Plan:
         return torch.empty(self.workspace_size(n_samples, batch), dtype=torch.uint8, device="cuda")
 
     @staticmethod
+    def _workspace(workspace):
+        """(device address, bytes) of a workspace, which must be a contiguous CUDA tensor (the
+        kernels write it; a host address there would fault the device)."""
+        import torch
+        if not (isinstance(workspace, torch.Tensor) and workspace.is_cuda
+                and workspace.is_contiguous()):
+            raise ValueError("workspace must be a contiguous CUDA tensor")
+        return workspace.data_ptr(), workspace.numel() * workspace.element_size()
+
+    @staticmethod
     def _shape(x):
         return (1, x.shape[0]) if x.dim() == 2 else (x.shape[0], x.shape[1])
 
@@ -248,9 +258,10 @@ class Plan:
         if out is None:
             out = torch.empty_like(x)
         self._field(out, "out", like=x)
+        ws_ptr, ws_bytes = self._workspace(workspace)
         _check(_lib.cbessfm_backpropagate_checkpointed(
-            self._h, x.data_ptr(), out.data_ptr(), L, batch, workspace.data_ptr(),
-            workspace.numel(), _stream_handle(stream)))
+            self._h, x.data_ptr(), out.data_ptr(), L, batch, ws_ptr, ws_bytes,
+            _stream_handle(stream)))
         return out
 
     def grad(self, grad_out, workspace, want_input: bool = True, want_ratio: bool = True,
@@ -262,6 +273,7 @@ class Plan:
         if not (isinstance(grad_out, torch.Tensor) and grad_out.is_cuda
                 and grad_out.dtype == torch.complex64):
             raise ValueError("grad_out must be a complex64 CUDA tensor")
+        ws_ptr, ws_bytes = self._workspace(workspace)
         # temporaries and outputs are made on the call's stream, so their fills and their
         # memory's reuse are ordered with the kernels (a no-op without an explicit stream)
         with torch.cuda.stream(stream):
@@ -274,8 +286,7 @@ class Plan:
             _check(_lib.cbessfm_grad(self._h, g.data_ptr(), gc.data_ptr() if gc.numel() else None,
                                      gr.data_ptr() if gr is not None else None,
                                      gi.data_ptr() if gi is not None else None,
-                                     workspace.data_ptr(), workspace.numel(), L, batch,
-                                     _stream_handle(stream)))
+                                     ws_ptr, ws_bytes, L, batch, _stream_handle(stream)))
         return gc, gr, gi
 
     def set_coeffs(self, coeffs, stream=None):
@@ -325,10 +336,9 @@ class Plan:
                 out = torch.empty_like(x)
             if workspace is None and need:
                 workspace = torch.empty(need, dtype=torch.uint8, device=x.device)
+            ws_ptr, ws_bytes = self._workspace(workspace) if workspace is not None else (None, 0)
             _check(_lib.cbessfm_backpropagate_streamed(
-                self._h, x.data_ptr(), out.data_ptr(),
-                workspace.data_ptr() if workspace is not None else None,
-                workspace.numel() if workspace is not None else 0, L, batch,
+                self._h, x.data_ptr(), out.data_ptr(), ws_ptr, ws_bytes, L, batch,
                 _stream_handle(stream)))
         return out
 

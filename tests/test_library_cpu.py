@@ -262,3 +262,12 @@ def test_set_coeffs_checks_the_tap_shape(lib):
     for shape in [(2, 3, 3, 3), (1, 3, 3, 5), (90,)]:
         with pytest.raises(ValueError, match=r"coeffs must have shape \(2, 3, 3, 5\)"):
             plan.set_coeffs(np.zeros(shape, np.float32))
+
+
+def test_workspace_must_be_device_memory(lib):
+    """A workspace is written by the kernels: a host tensor (whose address would fault the
+    device) or a strided view is refused before the library call."""
+    import torch
+    for ws in [torch.zeros(256, dtype=torch.uint8), torch.zeros(512, dtype=torch.uint8)[::2]]:
+        with pytest.raises(ValueError, match="workspace must be a contiguous CUDA tensor"):
+            lib.Plan._workspace(ws)
