@@ -52,10 +52,14 @@ def overlap_for(shape: JobShape) -> int:
     return max(16, int(math.ceil(per_sb / 16.0)) * 16)
 
 
+# Most subbands the chain kernel takes at each N' (one block's field, exchange arrays and
+# intensity rows in one CTA's shared memory); the library's plan_create refuses larger ones.
+MAX_BANDS = {2048: 5, 1024: 5, 512: 10, 256: 16}
+
+
 def _block_fits(n_fft: int, n_sb: int) -> bool:
-    """Whether the chain kernel takes N' = n_fft with n_sb subbands in one CTA (threads and
-    shared memory per block)."""
-    return not (n_fft == 2048 and n_sb > 5) and not (n_fft == 1024 and n_sb > 10)
+    """Whether the chain kernel takes N' = n_fft with n_sb subbands in one CTA."""
+    return n_sb <= MAX_BANDS.get(n_fft, 16)
 
 
 def candidates(shape: JobShape):

@@ -38,8 +38,8 @@ def test_candidates_respect_overlap_taps_and_block_limits():
     assert 2048 not in [nf for nf, _ in autotune.candidates(_shape(n_sb=6))]
     # memory longer than any block: the largest block that fits, overlap capped at 3/4 of it
     assert autotune.candidates(_shape(L=5000e3)) == [(2048, 1536)]
-    assert autotune.candidates(_shape(n_sb=6, L=50000e3)) == [(1024, 768)]
-    assert autotune.candidates(_shape(n_sb=12, L=50000e3)) == [(512, 384)]
+    assert autotune.candidates(_shape(n_sb=6, L=50000e3)) == [(512, 384)]
+    assert autotune.candidates(_shape(n_sb=12, L=50000e3)) == [(256, 192)]
     with pytest.raises(ValueError, match="taps"):
         autotune.candidates(_shape(ntaps=1025))
     with pytest.raises(ValueError, match="mode"):
@@ -68,3 +68,27 @@ def test_measured_choice_is_read_back_from_the_cache(tmp_path):
     tuner = autotune.Autotuner("measure", cache_path=str(path))
     assert tuner.choose(s) == (512, 144)                    # no launch needed for a cached shape
     assert s.key() != _shape(n_sb=3, n_st=4, L=80e3, R=192e9, ntaps=7).key()
+
+
+def test_block_limits_agree_with_the_library():
+    """The tuner's subband limits per N' are exactly the plans the library accepts.  plan_create
+    checks threads and shared memory before touching the device, so without a GPU an accepted
+    plan fails later with CBESSFM_ERR_CUDA and a refused one returns CBESSFM_ERR_UNSUPPORTED."""
+    import ctypes
+    import numpy as np
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2409_14489_gb300 import cbessfm as cb
+    L = cb.lib()
+    link = cb.make_link(-21.7e-27, 80e3, 1, 64e9)
+    for nf in autotune.CANDIDATE_NFFT:
+        for n_sb in range(1, 17):
+            taps = np.zeros((1, n_sb, n_sb, 11), np.float32)
+            h = ctypes.c_void_p()
+            st = L.cbessfm_plan_create(ctypes.byref(link), n_sb, 1, 0.5,
+                                       taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 11,
+                                       nf, nf // 4, 0, ctypes.byref(h))
+            if st == cb.OK:
+                L.cbessfm_plan_destroy(h)
+            assert st in (cb.OK, cb.ERR_CUDA, cb.ERR_UNSUPPORTED), (nf, n_sb, st)
+            assert (st != cb.ERR_UNSUPPORTED) == autotune._block_fits(nf, n_sb), (nf, n_sb)
