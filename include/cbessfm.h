@@ -87,7 +87,9 @@ typedef struct cbessfm_plan cbessfm_plan;
  *   out       receives the plan.
  * Synchronous.  Builds the FP64-derived tables (GVD phases reduced modulo 2 pi, FFT twiddles)
  * on the current device.  Returns INVALID_ARG for out-of-range values, UNSUPPORTED when the
- * block does not fit one SM's shared memory.
+ * block does not fit one SM's shared memory: complex64 plans take up to 5 subbands at
+ * n_fft = 1024 or 2048, 10 at 512 and 16 at 256 or less, for any ntaps.  These checks run
+ * before the first CUDA call.
  */
 cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int steps, double ratio,
                                    const float* coeffs, int ntaps, int n_fft, int overlap,
