@@ -101,3 +101,33 @@ def test_zero_steps_adjoint_is_conjugate_dispersion():
                            np.zeros((0, 2, 2, 5)))
     np.testing.assert_allclose(G_in, dbp.cbessfm_block(G, pinv), atol=1e-12)
     assert gr == 0.0
+
+
+def test_per_pol_fir_adjoint_equals_its_sum_difference_form():
+    """The adjoint of the per-polarization FIR (weights (1, 1) on the own band, (2, 1)/1.5 and
+    (1, 2)/1.5 on the others, Eqs. (NLPR_polx), (NLPR_poly)) rewritten with S = G_tx + G_ty and
+    D = G_tx - G_ty: G_Px/y,l = sum_i corr(w_il, S_i) +/- (1/3) sum_{i != l} corr(w_il, D_i),
+    dL/dw_il[m] = sum_k S_i[k] (Px + Py)_l[k - m] + [i != l] (1/3) sum_k D_i[k] (Px - Py)_l[k - m]."""
+    from oracle import adjoint as oa
+    rng = np.random.default_rng(21)
+    n_sb, n, ntaps = 3, 32, 5
+    nc = ntaps // 2
+    Px, Py = rng.random((n_sb, n)), rng.random((n_sb, n))
+    G_tx, G_ty = rng.standard_normal((n_sb, n)), rng.standard_normal((n_sb, n))
+    w = rng.standard_normal((n_sb, n_sb, ntaps))
+    G_Px, G_Py, G_w = oa._fir_adjoint_per_pol(G_tx, G_ty, Px, Py, w)
+    S, D = G_tx + G_ty, G_tx - G_ty
+    want_x, want_y, want_w = np.zeros_like(Px), np.zeros_like(Py), np.zeros_like(w)
+    for i in range(n_sb):
+        for l in range(n_sb):
+            cross = 1.0 / 3.0 if i != l else 0.0
+            for m in range(-nc, nc + 1):
+                s_term = w[i, l, m + nc] * np.roll(S[i], -m)
+                d_term = cross * w[i, l, m + nc] * np.roll(D[i], -m)
+                want_x[l] += s_term + d_term
+                want_y[l] += s_term - d_term
+                want_w[i, l, m + nc] = (np.sum(S[i] * np.roll(Px[l] + Py[l], m))
+                                        + cross * np.sum(D[i] * np.roll(Px[l] - Py[l], m)))
+    np.testing.assert_allclose(G_Px, want_x, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(G_Py, want_y, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(G_w, want_w, rtol=0, atol=1e-12)
