@@ -5,7 +5,9 @@ PyTorch provides device memory and streams.  Importing this module loads the lib
 ``ImportError`` if it has not been built -- there is no CPU fallback.
 
 Field tensors are complex64 of shape ``(L, 2)`` or ``(batch, L, 2)`` (polarization-minor), which
-is exactly the library's float4-per-sample layout.
+is exactly the library's float4-per-sample layout; plans with FP16/BF16 storage take float16 /
+bfloat16 tensors of shape ``(L, 4)`` or ``(batch, L, 4)`` holding (x.re, x.im, y.re, y.im).
+Every call checks its fields' dtype, shape and memory before the library reads them.
 """
 from __future__ import annotations
 
