@@ -318,6 +318,18 @@ cbessfm_status cbessfm_set_nlpr_mode(cbessfm_plan* plan, int per_polarization);
  */
 cbessfm_status cbessfm_get_status(const cbessfm_plan* plan, cbessfm_stream stream);
 
+/*
+ * cbessfm_measure_fp32_peak -- a measurement utility, not an operation of the paper: the FP32
+ * fused multiply-add rate of the current device, the denominator of the chain kernels' ALU
+ * roofline.  A kernel of independent FFMA chains fills every SM (2048 threads each) and is
+ * timed with CUDA events on `stream`; *flops = 2 x FFMA lane operations per second of the
+ * fastest of `repeats` launches (1..1000; one untimed launch runs first), *sm_count = the
+ * device's SM count.  Synchronous: it waits for `stream`.  CBESSFM_ERR_INVALID_ARG for NULL
+ * outputs or repeats out of range, CBESSFM_ERR_CUDA if a launch or event call fails.
+ */
+cbessfm_status cbessfm_measure_fp32_peak(int repeats, double* flops, int* sm_count,
+                                         cbessfm_stream stream);
+
 /* Thread-local description of the last error returned on this thread ("" if none). */
 const char* cbessfm_last_error(void);
 

@@ -101,6 +101,9 @@ def _load():
     lib.cbessfm_analytic_taps.argtypes = [ctypes.POINTER(LinkStruct), c_int, c_int, c_int,
                                           c_void_p, c_int, c_int, c_void_p, c_void_p]
     lib.cbessfm_analytic_taps.restype = c_int
+    lib.cbessfm_measure_fp32_peak.argtypes = [c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_int),
+                                              c_void_p]
+    lib.cbessfm_measure_fp32_peak.restype = c_int
     return lib
 
 
@@ -373,6 +376,15 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def measure_fp32_peak(repeats: int = 10, stream=None):
+    """Measured FP32 FMA rate of the current device (``cbessfm_measure_fp32_peak``): returns
+    ``(flop_per_s, sm_count)``, best of ``repeats`` timed launches.  Synchronous."""
+    flops, sms = ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(_lib.cbessfm_measure_fp32_peak(int(repeats), ctypes.byref(flops), ctypes.byref(sms),
+                                          _stream_handle(stream)))
+    return flops.value, sms.value
 
 
 def version() -> str:

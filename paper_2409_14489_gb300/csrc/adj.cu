@@ -38,9 +38,9 @@ template <int E>
 __device__ __forceinline__ void fir8_acc(const ChainArgs& a, const float4* __restrict__ wbase,
                                          const float* __restrict__ rows0, int k0, float (&acc)[8]) {
     if (a.nchunks == 3) {
-        fir8<E, 3>(a, wbase, rows0, k0, acc);
+        fir8<E, 3>(a, wbase, rows0, a.pstride, k0, acc);
     } else {
-        fir8<E, 0>(a, wbase, rows0, k0, acc);
+        fir8<E, 0>(a, wbase, rows0, a.pstride, k0, acc);
     }
 }
 
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     {
         // DEMUX as in the forward chain: W_N^(K r) = W_N^(K_0 r) times the slot factor of (r, t)
         const float2* eb = reinterpret_cast<const float2*>(region) + p;
-        const float2* td = a.mix_tw + (size_t)n_sb * N;
+        const float2* td = a.mix_td;
         int K0 = ci + j;
         K0 += (K0 < 0) ? N : 0;
 #pragma unroll
@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
         __syncthreads();
         // MUX as in the forward chain: W_N^(K gi) = W_N^((j + NP q) gi) W_N^((N'/E) t gi)
         const float2* wr = a.mix_tw + (size_t)gi * N;
-        const float2* tm = a.mix_tw + (size_t)n_sb * (N + E) + gi * E;
+        const float2* tm = a.mix_tm + gi * E;
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
         for (int q = 0; q < n_sb; ++q) {
@@ -699,6 +699,7 @@ cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, doub
     const Layout l = layout(*p, n_samples, batch);
     unsigned char* ws = static_cast<unsigned char*>(workspace);
     ChainArgs a = make_chain_args(*p);
+    classic_tables(*p, a);                  // the adjoint runs the fft_slots plan
     a.L = n_samples;
     a.batch = batch;
     a.n_blocks = (int)blocks_for(n_samples, p->V);

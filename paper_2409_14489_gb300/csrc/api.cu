@@ -44,12 +44,44 @@ namespace {
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// exp(j ang) rounded to a float pair whose norm stays as close to 1 as float spacing allows.
+// The nearest floats to (cos, sin) can miss |w| = 1 by 6e-8; the chain multiplies by the same
+// table entries in every step, so that gain error adds up coherently over the steps (an FP32
+// emulation of a 15-step chain of 1024-point transforms: rel-L2 7.3e-6 with nearest-rounded
+// constants, 2.8e-6 with norm-preserving ones).  Candidates within 3 float steps of the nearest
+// pair; the norm error is weighed against one tenth of the phase error.
+float2 unit_f32(double ang) {
+    const double c = std::cos(ang), s = std::sin(ang);
+    const float c0 = (float)c, s0 = (float)s;
+    float bc = c0, bs = s0;
+    double best = -1.0;
+    float ci = c0;
+    for (int i = 0; i < 3; ++i) ci = std::nextafter(ci, -2.0f);
+    for (int i = -3; i <= 3; ++i, ci = std::nextafter(ci, 2.0f)) {
+        float sj = s0;
+        for (int j = 0; j < 3; ++j) sj = std::nextafter(sj, -2.0f);
+        for (int j = -3; j <= 3; ++j, sj = std::nextafter(sj, 2.0f)) {
+            const double dc = ci, ds = sj;
+            const double norm_err = std::fabs(dc * dc + ds * ds - 1.0);
+            const double phase_err = std::fabs(ds * c - dc * s);   // sin of the angle error
+            const double key = norm_err + 0.1 * phase_err;
+            if (best < 0.0 || key < best) {
+                best = key;
+                bc = ci;
+                bs = sj;
+            }
+        }
+    }
+    return make_float2(bc, bs);
+}
+
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 void free_plan(PlanImpl& p) {
     cudaFree(p.d_gvd);
     cudaFree(p.d_gvd_half);
     cudaFree(p.d_mix_tw);
+    if (p.d_fft_tw_cl != p.d_fft_tw) cudaFree(p.d_fft_tw_cl);
     cudaFree(p.d_fft_tw);
     cudaFree(p.d_taps);
     cudaFree(p.d_rot);
@@ -59,6 +91,7 @@ void free_plan(PlanImpl& p) {
     p.d_gvd_half = nullptr;
     p.d_mix_tw = nullptr;
     p.d_fft_tw = nullptr;
+    p.d_fft_tw_cl = nullptr;
     p.d_taps = nullptr;
     p.d_rot = nullptr;
     p.d_taps_t = nullptr;
@@ -76,15 +109,18 @@ std::vector<float> pack_taps(const PlanImpl& p, const float* coeffs) {
 
 }  // namespace
 
-int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands, int extra_bytes) {
-    // about 256 threads, whole warps (G * tb multiple of 32), shared memory and named-barrier
-    // ids (1 + g * bands + i <= 15 when groups span more than one warp)
+int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands, int extra_bytes,
+                          int max_threads, int min_ctas) {
+    // about 256 threads, whole warps (G * tb multiple of 32), shared memory (a share of the SM
+    // when the kernel is built for several CTAs per SM) and named-barrier ids
+    // (1 + g * bands + i <= 15 when groups span more than one warp)
     int granule = 1;
     while ((granule * tb) % 32 != 0) granule *= 2;
     int G = std::max(granule, (256 / tb) / granule * granule);
     G = std::min(G, kMaxG);
+    const int smem_cap = min_ctas > 1 ? (228 * 1024) / min_ctas - 1024 - 4096 : kMaxDynSmem;
     auto fits = [&](int g) {
-        return g * region_bytes + extra_bytes <= kMaxDynSmem && g * tb <= kMaxThreads &&
+        return g * region_bytes + extra_bytes <= smem_cap && g * tb <= max_threads &&
                !(2 * tpf > 32 && g * bands > 15);
     };
     while (G > granule && !fits(G)) G -= granule;
@@ -92,17 +128,51 @@ int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands, int extr
 }
 
 // OLS blocks resident per SM for G blocks of `tb` threads per CTA and `region` bytes each: the
-// forward kernels are compiled for 640 threads at 96 registers, so registers bound the CTAs too.
-int resident_blocks(int G, int tb, int region, int tables) {
+// forward kernels are compiled for `max_threads` threads and `min_ctas` CTAs per SM, which sets
+// their registers per thread (96 for 640 x 1 and 320 x 2), so registers bound the CTAs too.
+int resident_blocks(int G, int tb, int region, int tables, int max_threads, int min_ctas) {
     if (G < 1) return 0;
-    const int smem_per_cta = G * region + tables + 4096;         // + static shared memory
+    const int smem_per_cta = G * region + tables + 4096 + 1024;  // + static and reserved
     const int by_smem = (228 * 1024) / smem_per_cta;
-    const int by_regs = 65536 / (G * tb * 96);
+    const int regs = std::min(255, 65536 / (max_threads * min_ctas)) / 8 * 8;
+    const int by_regs = 65536 / (G * tb * regs);
     return G * std::min(by_smem, by_regs);
 }
 
 bool choose_layout(PlanImpl& p, int tb, int tpf) {
     const int bands = p.n_sb, n_fft = p.n_fft;
+    const bool per_pol = p.per_pol != 0;
+    const int E = chain_slots(n_fft, per_pol);
+    const int max_threads = chain_max_threads(n_fft, per_pol);
+    const int min_ctas = chain_min_ctas(n_fft, per_pol);
+    // per-CTA tables: FFT twiddles always, one step's taps (double-buffered) for 9 to 12 taps
+    const int tw = chain_tw_bytes(fft_tw_size(n_fft, E));
+    const int tw_taps = tw + (p.nchunks == 3 ? chain_taps_bytes(bands) : 0);
+    if (chain_packed(n_fft, per_pol)) {
+        // one exchange array per group; its intensity row, (cos, sin) row (one spare per 32) and
+        // the parked slots fit inside it
+        const int xl_bytes = 16 * xpad_len_s(n_fft, fft_xsh(n_fft, E));
+        if (4 * p.pstride + 8 * (n_fft + n_fft / 32) + 8 * kParkSlots * 2 * tpf > xl_bytes)
+            return false;
+        const int region = round_up(bands * xl_bytes, 128);
+        int tbl = tw_taps;
+        int G = choose_blocks_per_cta(tb, region, tpf, bands, tbl, max_threads, min_ctas);
+        if (G < 1 && tbl != tw) {
+            tbl = tw;
+            G = choose_blocks_per_cta(tb, region, tpf, bands, tbl, max_threads, min_ctas);
+        }
+        if (G < 1) return false;
+        p.tbl_bytes = tbl;
+        p.taps_smem = tbl != tw ? 1 : 0;
+        p.layout = kLayoutPacked;
+        p.region_bytes = region;
+        p.nlpr_off = 0;
+        p.exb_off = 0;
+        p.pbuf_bytes = 0;
+        p.G = G;
+        p.threads = G * tb;
+        return true;
+    }
     const int exch = round_up(std::max(16 * p.N, 16 * xpad_len(p.N)), 128);  // staging fits too
     const int prow = round_up(4 * bands * p.pstride, 128);
     const int csr = round_up(8 * bands * xpad_len(n_fft), 128);
@@ -134,20 +204,17 @@ bool choose_layout(PlanImpl& p, int tb, int tpf) {
         for (int k = 0; k < 4; ++k)
             if (std::strcmp(env, names[k]) == 0) forced = k;
     }
-    // per-CTA tables: FFT twiddles always, one step's taps (double-buffered) for 9 to 12 taps
-    const int tw = chain_tw_bytes(fft_tw_size(n_fft));
-    const int tw_taps = tw + (p.nchunks == 3 ? chain_taps_bytes(bands) : 0);
     int best = -1, best_res = 0, best_G = 0, best_tbl = 0;
     for (int k = 0; k < 4; ++k) {
         const Cand& c = cands[k];
         int tbl = tw_taps;
-        int G = choose_blocks_per_cta(tb, c.region, tpf, bands, tbl);
+        int G = choose_blocks_per_cta(tb, c.region, tpf, bands, tbl, max_threads, min_ctas);
         if (G < 1 && tbl != tw) {
             tbl = tw;
-            G = choose_blocks_per_cta(tb, c.region, tpf, bands, tbl);
+            G = choose_blocks_per_cta(tb, c.region, tpf, bands, tbl, max_threads, min_ctas);
         }
         if (G < 1) continue;
-        const int res = resident_blocks(G, tb, c.region, tbl);
+        const int res = resident_blocks(G, tb, c.region, tbl, max_threads, min_ctas);
         if (k == forced) {
             best = k;
             best_G = G;
@@ -203,11 +270,25 @@ ChainArgs make_chain_args(const PlanImpl& p) {
     a.gvd_first = p.d_gvd_half;
     a.gvd_last = p.d_gvd_half + 2 * (p.N / 2 + 1);
     a.mix_tw = p.d_mix_tw;
-    a.fft_tw = p.d_fft_tw;
+    {
+        const int ef = chain_slots(p.n_fft, false);
+        a.mix_td = p.d_mix_tw + (size_t)p.n_sb * p.N;
+        a.mix_tm = a.mix_td + (size_t)p.n_sb * ef;
+        a.fft_tw = p.d_fft_tw;
+    }
     a.taps = p.d_taps;
     a.rot_tbl = p.d_rot;
     a.status = p.d_status;
+    a.wait_cycles = p.wait_cycles;
+    if (p.per_pol) classic_tables(p, a);
     return a;
+}
+
+void classic_tables(const PlanImpl& p, ChainArgs& a) {
+    const int ef = chain_slots(p.n_fft, false), ec = fft_slots(p.n_fft);
+    a.mix_td = p.d_mix_tw + (size_t)p.n_sb * p.N + 2 * (size_t)p.n_sb * ef;
+    a.mix_tm = a.mix_td + (size_t)p.n_sb * ec;
+    a.fft_tw = p.d_fft_tw_cl;
 }
 
 const PlanImpl* plan_impl(const cbessfm_plan* plan) { return plan ? &plan->impl : nullptr; }
@@ -305,10 +386,11 @@ static cbessfm_status plan_create_body(const cbessfm_link* link, int bands, int 
     p.p_off = ((3 - p.nc) % 4 + 4) % 4;
     p.pstride = round_up(n_fft + 2 * p.H + 8, 32);   // rows start on 128-byte boundaries
 
-    const int tpf = n_fft / fft_slots(n_fft);
+    const int tpf = n_fft / chain_slots(n_fft, false);
     const int tb = 2 * bands * tpf;                 // one polarization per thread
-    if (tb > kMaxThreads)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "%d threads per block exceed %d", tb, kMaxThreads);
+    if (tb > chain_max_threads(n_fft, false))
+        return fail(CBESSFM_ERR_UNSUPPORTED, "%d threads per block exceed %d", tb,
+                    chain_max_threads(n_fft, false));
     if (!choose_layout(p, tb, tpf))
         return fail(CBESSFM_ERR_UNSUPPORTED, "no shared-memory layout fits bands = %d, n_fft = %d",
                     bands, n_fft);
@@ -317,42 +399,52 @@ static cbessfm_status plan_create_body(const cbessfm_link* link, int bands, int 
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
 
     // ---- FP64 tables on the host: FFT pass twiddles and DEMUX/MUX twiddles -------------------
-    std::vector<float2> fft_tw(std::max(1, fft_tw_size(n_fft)));
+    // FFT pass twiddles of the plan of (n_fft, E): the Manakov forward chain's E and fft_slots
     const double two_pi = 6.283185307179586476925286766559;
-    for (int pass = 1; pass < fft_npasses(n_fft); ++pass) {
-        const int R = fft_radix(n_fft, pass), NS = fft_ns(n_fft, pass);
-        const int off = fft_tw_offset(n_fft, pass);
-        for (int r = 1; r < R; ++r)
-            for (int a = 0; a < NS; ++a) {
-                const long long num = (long long)a * r;           // < NS R
-                const double ang = -two_pi * (double)num / (double)(NS * R);
-                fft_tw[off + (r - 1) * NS + a] = make_float2((float)std::cos(ang), (float)std::sin(ang));
-            }
-    }
-    // [bands][N] W_N^(K r), then the per-slot factors of the chain's DEMUX and MUX:
+    auto pass_twiddles = [&](int E) {
+        std::vector<float2> tw(std::max(1, fft_tw_size(n_fft, E)));
+        for (int pass = 1; pass < fft_npasses(n_fft, E); ++pass) {
+            const int R = fft_radix(n_fft, E, pass), NS = fft_ns(n_fft, E, pass);
+            const int off = fft_tw_offset(n_fft, E, pass);
+            for (int r = 1; r < R; ++r)
+                for (int a = 0; a < NS; ++a) {
+                    const long long num = (long long)a * r;           // < NS R
+                    const double ang = -two_pi * (double)num / (double)(NS * R);
+                    tw[off + (r - 1) * NS + a] = unit_f32(ang);
+                }
+        }
+        return tw;
+    };
+    const int Ef = chain_slots(n_fft, false), Ec = fft_slots(n_fft);
+    const bool same_plan = Ef == Ec;
+    const std::vector<float2> fft_tw = pass_twiddles(Ef);
+    const std::vector<float2> fft_tw_cl = same_plan ? std::vector<float2>() : pass_twiddles(Ec);
+    // [bands][N] W_N^(K r), then the per-slot factors of the chain's DEMUX and MUX for the
+    // forward chain's E, then for fft_slots' E:
     // [bands][E] W_N^(r (N'/E) t) times W_N^(-r N') for t >= E/2 (DEMUX), [bands][E] W_N^(r (N'/E) t)
-    const int E = fft_slots(n_fft), TPF = n_fft / E;
-    std::vector<float2> mix_tw((size_t)bands * p.N + 2 * (size_t)bands * E);
+    std::vector<float2> mix_tw((size_t)bands * p.N + 2 * (size_t)bands * (Ef + Ec));
     auto w_n = [&](long long num) {                  // W_N^num, exponent reduced exactly mod N
         num %= p.N;
         if (num < 0) num += p.N;
-        const double ang = -two_pi * (double)num / (double)p.N;
-        return make_float2((float)std::cos(ang), (float)std::sin(ang));
+        return unit_f32(-two_pi * (double)num / (double)p.N);
     };
     for (int r = 0; r < bands; ++r)
         for (int K = 0; K < p.N; ++K) mix_tw[(size_t)r * p.N + K] = w_n((long long)K * r);
-    float2* const mix_td = mix_tw.data() + (size_t)bands * p.N;
-    float2* const mix_tm = mix_td + (size_t)bands * E;
-    for (int r = 0; r < bands; ++r)
-        for (int t = 0; t < E; ++t) {
-            mix_td[r * E + t] = w_n((long long)r * (TPF * t - (t >= E / 2 ? n_fft : 0)));
-            mix_tm[r * E + t] = w_n((long long)r * TPF * t);
-        }
+    auto slot_factors = [&](float2* mix_td, int E) {
+        const int TPF = n_fft / E;
+        float2* const mix_tm = mix_td + (size_t)bands * E;
+        for (int r = 0; r < bands; ++r)
+            for (int t = 0; t < E; ++t) {
+                mix_td[r * E + t] = w_n((long long)r * (TPF * t - (t >= E / 2 ? n_fft : 0)));
+                mix_tm[r * E + t] = w_n((long long)r * TPF * t);
+            }
+    };
+    slot_factors(mix_tw.data() + (size_t)bands * p.N, Ef);
+    slot_factors(mix_tw.data() + (size_t)bands * p.N + 2 * (size_t)bands * Ef, Ec);
 
     std::vector<float2> rot(256);
     for (int k = 0; k < 256; ++k) {
-        const double ang = two_pi * k / 256.0;
-        rot[k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        rot[k] = unit_f32(two_pi * k / 256.0);
     }
     // every host container exists before the first device allocation (see abi_guard.h)
     const std::vector<float> packed = steps > 0 ? pack_taps(p, coeffs) : std::vector<float>();
@@ -370,6 +462,13 @@ static cbessfm_status plan_create_body(const cbessfm_link* link, int bands, int 
     CB_TRY(cudaMalloc(&p.d_gvd_half, sizeof(float2) * 4 * (p.N / 2 + 1)), "cudaMalloc(gvd half)");
     CB_TRY(cudaMalloc(&p.d_mix_tw, sizeof(float2) * mix_tw.size()), "cudaMalloc(mix)");
     CB_TRY(cudaMalloc(&p.d_fft_tw, sizeof(float2) * fft_tw.size()), "cudaMalloc(fft tw)");
+    if (same_plan) {
+        p.d_fft_tw_cl = p.d_fft_tw;
+    } else {
+        CB_TRY(cudaMalloc(&p.d_fft_tw_cl, sizeof(float2) * fft_tw_cl.size()), "cudaMalloc(fft tw)");
+        CB_TRY(cudaMemcpy(p.d_fft_tw_cl, fft_tw_cl.data(), sizeof(float2) * fft_tw_cl.size(),
+                          cudaMemcpyHostToDevice), "copy fft twiddles");
+    }
     CB_TRY(cudaMalloc(&p.d_taps, sizeof(float) * n_taps_dev), "cudaMalloc(taps)");
     CB_TRY(cudaMalloc(&p.d_taps_t, sizeof(float) * n_taps_dev), "cudaMalloc(transposed taps)");
     CB_TRY(cudaMalloc(&p.d_status, sizeof(unsigned int)), "cudaMalloc(status)");
@@ -547,7 +646,7 @@ static cbessfm_status set_nlpr_mode_body(cbessfm_plan* plan, int per_polarizatio
     if (p.per_pol == per_polarization) return CBESSFM_OK;
     PlanImpl trial = p;
     trial.per_pol = per_polarization;
-    const int tpf = p.n_fft / fft_slots(p.n_fft);
+    const int tpf = p.n_fft / chain_slots(p.n_fft, per_polarization != 0);
     const int tb = 2 * p.n_sb * tpf;
     if (!choose_layout(trial, tb, tpf))
         return fail(CBESSFM_ERR_UNSUPPORTED,

@@ -100,20 +100,25 @@ static cbessfm_status batch_create_body(const cbessfm_job* jobs, int njobs, cbes
         gr.n_sb = std::get<1>(kv.first);
         gr.storage = std::get<2>(kv.first);
         gr.per_pol = std::get<3>(kv.first);
-        const int tpf = gr.np / fft_slots(gr.np);
+        const bool pp = gr.per_pol != 0;
+        const int E = chain_slots(gr.np, pp);
+        const int tpf = gr.np / E;
         const int tb = 2 * gr.n_sb * tpf;
+        const int max_threads = chain_max_threads(gr.np, pp), min_ctas = chain_min_ctas(gr.np, pp);
         bool any_taps = false;
         for (int k : kv.second) {
             gr.region_bytes = std::max(gr.region_bytes, args[k].region_bytes);
             any_taps = any_taps || args[k].taps_smem;
         }
         // per-CTA tables: twiddles, plus the tap buffers if a job stages its taps and they fit
-        const int tw = chain_tw_bytes(fft_tw_size(gr.np));
+        const int tw = chain_tw_bytes(fft_tw_size(gr.np, E));
         gr.tbl_bytes = tw + (any_taps ? chain_taps_bytes(gr.n_sb) : 0);
-        gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb, gr.tbl_bytes);
+        gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb, gr.tbl_bytes, max_threads,
+                                     min_ctas);
         if (gr.G < 1 && any_taps) {
             gr.tbl_bytes = tw;
-            gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb, gr.tbl_bytes);
+            gr.G = choose_blocks_per_cta(tb, gr.region_bytes, tpf, gr.n_sb, gr.tbl_bytes,
+                                         max_threads, min_ctas);
         }
         if (gr.G < 1)
             return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape for n_fft %d, bands %d", gr.np, gr.n_sb);

@@ -20,6 +20,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -55,7 +57,6 @@ __device__ __forceinline__ float2 rotation_psi(float th, const float2* __restric
     const float2 tr = c_mul(t, make_float2(-0.5f * d2, d * fmaf(-0.16666666666666667f, d2, 1.0f)));
     return make_float2(tr.x + (t.x - 1.0f), tr.y + t.y);
 }
-constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz: never reached by a live copy
 
 // Barrier over the 2 NP/E threads (both polarizations) of one FFT group.  Groups of a warp or
 // less share their warp with other groups running the same code, so a warp barrier suffices.
@@ -106,8 +107,8 @@ __device__ __forceinline__ int pswz(int m) {
     constexpr int MASK = E == 16 ? 1 : 3;
     return m ^ (((m >> 5) & MASK) << 2);
 }
-// (cos, sin) rows carry one spare float2 per 16 so the 8-sample runs of adjacent lanes do not
-// collide on a bank.
+// (cos, sin) rows carry one spare float2 per 16 (per 32 in the packed layout) so the 8-sample
+// runs of adjacent lanes do not collide on a bank.
 __device__ __forceinline__ int cpad(int k) { return k + (k >> 4); }
 
 // Rotation factors for the 8 samples k = k0 .. k0 + 7 of subband i, step s:
@@ -121,38 +122,45 @@ __device__ __forceinline__ int cpad(int k) { return k + (k >> 4); }
 // WS: the taps `wbase` are in shared memory (plain loads) instead of global memory.
 // PAD1: the last 4-tap chunk holds one zero pad tap (ntaps = 4 NCH - 1, e.g. 11): its
 // multiply-adds are skipped (adding 0 * P leaves the sum unchanged bit for bit).
+// `rs`: floats from one row to the next.
 template <int E, int NCH, bool WS = false, bool PAD1 = false>
 __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restrict__ wbase,
-                                     const float* __restrict__ rows0, int k0, float (&acc)[8],
-                                     int skip_l = -1) {
+                                     const float* __restrict__ rows0, int rs, int k0,
+                                     float (&acc)[8], int skip_l = -1) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) acc[q] = 0.f;
     const int m0 = a.H + a.p_off + k0 + a.nc - 3;      // row index of chunk 0's window
     for (int l = 0; l < a.n_sb; ++l) {
         if (l == skip_l) continue;                     // uniform across the subband group
-        const float* pl = rows0 + l * a.pstride;
+        const float* pl = rows0 + l * rs;
         if constexpr (NCH > 0) {
+            // Chunk c reads the 11 window samples from 16-byte granule NCH - 1 - c on, so the
+            // chunks run with a sliding window of three granules: granules NCH + 1, NCH and
+            // NCH - 1 for chunk 0, then one more granule (lower) per chunk.  Only 12 window
+            // samples and one chunk's taps are live next to the accumulators.
             const float4* wrow = wbase + l * NCH;
-            float4 w4[NCH];
-#pragma unroll
-            for (int c = 0; c < NCH; ++c) w4[c] = WS ? wrow[c] : __ldg(wrow + c);
             const int m_lo = m0 - 4 * (NCH - 1);
-            float win[8 + 4 * NCH];
-#pragma unroll
-            for (int e = 0; e < 2 + NCH; ++e) {
-                const float4 v = *reinterpret_cast<const float4*>(pl + pswz<E>(m_lo + 4 * e));
-                win[4 * e] = v.x; win[4 * e + 1] = v.y; win[4 * e + 2] = v.z; win[4 * e + 3] = v.w;
-            }
+            auto granule = [&](int e) {
+                return *reinterpret_cast<const float4*>(pl + pswz<E>(m_lo + 4 * e));
+            };
+            float4 g0 = granule(NCH - 1), g1 = granule(NCH), g2 = granule(NCH + 1);
 #pragma unroll
             for (int c = 0; c < NCH; ++c) {
-                const int off = 4 * (NCH - 1 - c);
+                if (c > 0) {                               // slide down by one granule
+                    g2 = g1;
+                    g1 = g0;
+                    g0 = granule(NCH - 1 - c);
+                }
+                const float4 w4 = WS ? wrow[c] : __ldg(wrow + c);
+                const float win[12] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y,
+                                       g1.z, g1.w, g2.x, g2.y, g2.z, g2.w};
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     float t = acc[q];
-                    t = fmaf(w4[c].x, win[off + q + 3], t);   // m = -nc + 4c
-                    t = fmaf(w4[c].y, win[off + q + 2], t);   // m = -nc + 4c + 1
-                    t = fmaf(w4[c].z, win[off + q + 1], t);
-                    if (!(PAD1 && c == NCH - 1)) t = fmaf(w4[c].w, win[off + q], t);
+                    t = fmaf(w4.x, win[q + 3], t);   // m = -nc + 4c
+                    t = fmaf(w4.y, win[q + 2], t);   // m = -nc + 4c + 1
+                    t = fmaf(w4.z, win[q + 1], t);
+                    if (!(PAD1 && c == NCH - 1)) t = fmaf(w4.w, win[q], t);
                     acc[q] = t;
                 }
             }
@@ -186,20 +194,20 @@ __device__ __forceinline__ void fir8(const ChainArgs& a, const float4* __restric
 // `s_taps` is the step's tap buffer in shared memory when a.taps_smem is set.
 template <int E>
 __device__ __forceinline__ void fir8_any(const ChainArgs& a, const float* __restrict__ rows0,
-                                         const float4* __restrict__ s_taps, int s, int i, int k0,
-                                         float (&acc)[8], int skip_l) {
+                                         int rs, const float4* __restrict__ s_taps, int s, int i,
+                                         int k0, float (&acc)[8], int skip_l) {
     if (a.taps_smem) {
         if (a.ntaps_pad == 2 * a.nc + 2)                                     // 11 taps
-            fir8<E, 3, true, true>(a, s_taps + i * a.n_sb * 3, rows0, k0, acc, skip_l);
+            fir8<E, 3, true, true>(a, s_taps + i * a.n_sb * 3, rows0, rs, k0, acc, skip_l);
         else                                                                 // 9, 10, 12 taps
-            fir8<E, 3, true>(a, s_taps + i * a.n_sb * 3, rows0, k0, acc, skip_l);
+            fir8<E, 3, true>(a, s_taps + i * a.n_sb * 3, rows0, rs, k0, acc, skip_l);
     } else {
         const float4* wbase = reinterpret_cast<const float4*>(
             a.taps + (size_t)(s * a.n_sb + i) * a.n_sb * a.ntaps_pad);
         if (a.nchunks == 3) {
-            fir8<E, 3>(a, wbase, rows0, k0, acc, skip_l);
+            fir8<E, 3>(a, wbase, rows0, rs, k0, acc, skip_l);
         } else {
-            fir8<E, 0>(a, wbase, rows0, k0, acc, skip_l);
+            fir8<E, 0>(a, wbase, rows0, rs, k0, acc, skip_l);
         }
     }
 }
@@ -208,18 +216,19 @@ __device__ __forceinline__ void fir8_any(const ChainArgs& a, const float* __rest
 // two angles theta^x = theta + delta and theta^y = theta - delta, where theta is the Manakov
 // phase and delta = (1/3) sum_{l != i} w_il (Px_l - Py_l) (the D rows follow the P rows): with
 // w_il = (3/2) c_il, Eqs. (NLPR_polx/poly) weigh XPM by (2 Px + Py) / 1.5 and (Px + 2 Py) / 1.5.
-template <int E, bool PERPOL>
+// CSH: the (cos, sin) row has one spare float2 per 2^CSH.
+template <int E, bool PERPOL, int CSH = 4>
 __device__ __forceinline__ void nlpr_rotation8(const ChainArgs& a, const float* __restrict__ prow0,
-                                               float2* __restrict__ cs_row,
+                                               int rs, float2* __restrict__ cs_row,
                                                const float2* __restrict__ rot_tbl,
                                                const float4* __restrict__ s_taps, int s, int i,
                                                int k0) {
     float acc[8];
-    fir8_any<E>(a, prow0, s_taps, s, i, k0, acc, -1);
-    float2* dst = cs_row + cpad(k0);                   // k0 % 16 in {0, 8}: no carry below
+    fir8_any<E>(a, prow0, rs, s_taps, s, i, k0, acc, -1);
+    float2* dst = cs_row + k0 + (k0 >> CSH);           // k0 % 8 = 0: no carry below
     if constexpr (PERPOL) {
         float dl[8];
-        fir8_any<E>(a, prow0 + a.n_sb * a.pstride, s_taps, s, i, k0, dl, i);
+        fir8_any<E>(a, prow0 + a.n_sb * a.pstride, rs, s_taps, s, i, k0, dl, i);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const float d = dl[q] * (1.0f / 3.0f);
@@ -265,9 +274,9 @@ struct ThreadPos {
     int tid, TB, g, rem, p, gi, j;
 };
 
-template <int NP>
+template <int NP, int E = fft_slots(NP)>
 __device__ __forceinline__ ThreadPos thread_pos(int n_sb) {
-    constexpr int TPF = NP / fft_slots(NP);
+    constexpr int TPF = NP / E;
     ThreadPos t;
     t.tid = threadIdx.x;
     t.TB = 2 * n_sb * TPF;
@@ -285,6 +294,13 @@ __device__ __forceinline__ ThreadPos thread_pos(int n_sb) {
 // CTA call it together (it contains block-wide barriers); `real` = false runs a zero block and
 // stores nothing.  `bar_g` is the slot's mbarrier, used with phase `parity`.  Returns false if a
 // bounded wait for the staging copy gave up (the caller must then stop).
+//
+// E = chain_slots(NP, PERPOL) register slots per thread.  With the two-pass plan (N' = 1024, 32
+// slots) the block uses the packed layout (kLayoutPacked): one exchange array per subband
+// group, which between the inverse FFT's loads and the forward FFT's stores of a step also
+// holds the group's intensity row and then its (cos, sin) row.  That keeps a 5-subband block
+// under half of an SM's shared memory, so two CTAs share an SM and fill each other's barrier
+// phases.
 template <int NP, int ST, bool CKPT = false, bool PERPOL = false>
 __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* smem,
                                             int region_bytes, uint64_t* bar_g, uint32_t parity,
@@ -294,10 +310,16 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                                             bool real, int seq, int blk) {
     using S = Storage<ST>;
     using Pol = typename S::Pol;
-    constexpr int E = fft_slots(NP);                   // register slots per thread
+    constexpr int E = chain_slots(NP, PERPOL);         // register slots per thread
+    constexpr bool PACKED = chain_packed(NP, PERPOL);  // two-pass FFT, packed layout
+    constexpr int SH = fft_xsh(NP, E);                 // exchange padding: one per 2^SH
     constexpr int TPF = NP / E;                        // threads per (subband, polarization)
-    constexpr int XL = 2 * xpad_len(NP);               // float2 per group exchange array
-    constexpr int CSL = NP + NP / 16;                  // float2 per (cos, sin) row
+    constexpr int XL = 2 * xpad_len_s(NP, SH);         // float2 per group exchange array
+    constexpr int CSH = PACKED ? 5 : 4;                // (cos, sin) rows: one spare per 2^CSH
+    constexpr int CSL = NP + (NP >> CSH);              // float2 per (cos, sin) row
+    // DEMUX/MUX twiddles by one table value per polyphase row times a per-slot factor; 32 slots
+    // keep the plain table read: they leave no registers for the product
+    constexpr bool kFactor = E == 16;
     const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
     unsigned char* region = smem + (size_t)g * region_bytes;
     float2* const grpA = reinterpret_cast<float2*>(region) + gi * XL;   // this group's array A
@@ -307,8 +329,8 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     // two-pass FFTs use A for the inverse and B for the forward transform of a step.  The
     // (cos, sin) rows then live in the array the inverse FFT read last, which stays idle until
     // the forward FFT's second exchange (or the next step's inverse FFT).
-    constexpr int NPASS = fft_npasses(NP);
-    const bool pp = a.layout == kLayoutPingPong;
+    constexpr int NPASS = fft_npasses(NP, E);
+    const bool pp = !PACKED && a.layout == kLayoutPingPong;
     float2* const grpB = pp ? reinterpret_cast<float2*>(region + a.exb_off) + gi * XL : grpA;
     float2* const eB = grpB + p;
     float2* const inv1 = e;
@@ -362,15 +384,17 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         }
         bool ok = true;
         if (real) {
-            ok = mbar_wait_bounded(bar_g, parity, kWaitCycles);
+            ok = mbar_wait_bounded(bar_g, parity, a.wait_cycles);
         } else {
             float4* z = reinterpret_cast<float4*>(region);
             for (int n = rem; n < a.N; n += TB) z[n] = make_float4(0.f, 0.f, 0.f, 0.f);
-            ok = mbar_wait_bounded(bar_g, parity, kWaitCycles);
+            ok = mbar_wait_bounded(bar_g, parity, a.wait_cycles);
         }
         if (__syncthreads_or(!ok)) {
             if (!ok) atomicOr(a.status, kStatusTimeout);
-            if (real) mbar_wait_bounded(bar_g, parity, kWaitCycles);   // let in-flight copies land
+            // let in-flight copies land before the shared memory is given up (the default
+            // bound: a live copy always completes long before it)
+            mbar_wait_bounded(bar_g, parity, kWaitCycles);
             return false;
         }
     } else {
@@ -403,10 +427,10 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                 st8[n] = real ? __ldg(src + q) : make_uint2(0u, 0u);
             }
         }
-        const bool ok = mbar_wait_bounded(bar_g, parity, kWaitCycles);
+        const bool ok = mbar_wait_bounded(bar_g, parity, a.wait_cycles);
         if (__syncthreads_or(!ok)) {
             if (!ok) atomicOr(a.status, kStatusTimeout);
-            if (bulk) mbar_wait_bounded(bar_g, parity, kWaitCycles);
+            mbar_wait_bounded(bar_g, parity, kWaitCycles);
             return false;
         }
     }
@@ -420,7 +444,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     fft_regs<NP, E, false, true>(x, j, e, s_tw, bar);              // Y_r, r = gi
     bar();
 #pragma unroll
-    for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = x[t];
+    for (int t = 0; t < E; ++t) e[2 * xpad_s<SH>(j + TPF * t)] = x[t];
     __syncthreads();
     const int N = a.N;
     const int ci = -N / 2 + gi * NP + NP / 2;                      // centre bin of subband gi
@@ -430,7 +454,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         // N' for t >= E/2, so W_N^(K r) = W_N^(K_0 r) times a factor of (r, t) only: one table
         // load per r and thread, the factors from a small table read alike by the whole warp.
         const float2* eb = reinterpret_cast<const float2*>(region) + p;
-        const float2* td = a.mix_tw + (size_t)a.n_sb * N;                 // [n_sb][E]
+        const float2* td = a.mix_td;                                    // [n_sb][E]
         int K0 = ci + j;
         K0 += (K0 < 0) ? N : 0;
 #pragma unroll
@@ -443,11 +467,9 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                 const int kap = j + TPF * t;
                 int K = ci + (kap < NP / 2 ? kap : kap - NP);
                 K += (K < 0) ? N : 0;
-                // E = 32 (N' = 2048) keeps the plain table read: its 32 slots leave no registers
-                // for the product
-                const float2 w = E == 16 ? c_mul(w0, __ldg(td + r * E + t))
+                const float2 w = kFactor ? c_mul(w0, __ldg(td + r * E + t))
                                          : __ldg(a.mix_tw + (size_t)r * N + K);
-                x[t] = c_add(x[t], c_mul(er[2 * xpad(K & (NP - 1))], w));
+                x[t] = c_add(x[t], c_mul(er[2 * xpad_s<SH>(K & (NP - 1))], w));
             }
         }
     }
@@ -457,14 +479,22 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     const int half_len = a.N / 2 + 1;
     gvd_apply<NP, E>(x, a.gvd_first, j, ci);                       // first GVD (x 1/N)
     save_ckpt(0, x);
-    // intensity rows and (cos, sin) rows: see the kLayout* constants
-    const bool alias = a.layout == kLayoutAlias;
-    float* const prowA = reinterpret_cast<float*>(region + a.nlpr_off);
+    // intensity rows and (cos, sin) rows: see the kLayout* constants.  Packed layout: the row of
+    // subband l at the start of exchange array l (rows 2 XL floats apart), the group's (cos, sin)
+    // row right after its own intensity row.
+    const bool alias = !PACKED && a.layout == kLayoutAlias;
+    float* const prowA = PACKED ? reinterpret_cast<float*>(region)
+                                : reinterpret_cast<float*>(region + a.nlpr_off);
+    const int rs = PACKED ? 2 * XL : a.pstride;                    // floats between rows
     float2* const cs_row =
-        pp ? (NPASS > 2 ? grpB : grpA)
-           : reinterpret_cast<float2*>(prowA + (PERPOL ? 2 : 1) * a.n_sb * a.pstride) + gi * CSL;
+        PACKED ? reinterpret_cast<float2*>(reinterpret_cast<float*>(grpA) + a.pstride)
+        : pp   ? (NPASS > 2 ? grpB : grpA)
+               : reinterpret_cast<float2*>(prowA + (PERPOL ? 2 : 1) * a.n_sb * a.pstride) + gi * CSL;
     const bool group_cs_bar = pp && a.pbuf_bytes > 0;
-    const int cs_base = (TPF >= 16) ? cpad(j) : 0;
+    const int cs_base = (TPF >= (1 << CSH)) ? j + (j >> CSH) : 0;
+    // packed layout: parked slots after the group's (cos, sin) row, [kParkSlots][2 TPF] float2
+    float2* const park = reinterpret_cast<float2*>(reinterpret_cast<float*>(grpA) + a.pstride) +
+                         CSL + (2 * j + p);
     const int n4 = a.n_sb * a.n_sb * 3;               // float4 per step's taps (12 per row)
 #pragma unroll 1
     for (int s = 0; s < a.n_st; ++s) {
@@ -476,20 +506,25 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
             for (int k = threadIdx.x; k < n4; k += blockDim.x) cp_async16(taps_buf + k, src + k);
             cp_async_commit();
         }
-        fft_regs<NP, E, true, true>(x, j, inv1, inv2, s_tw, bar, !pp); // subband time samples
+        // subband time samples; the packed layout's single array needs the barrier before the
+        // first store (the previous forward FFT's loads)
+        fft_regs<NP, E, true, true>(x, j, inv1, inv2, s_tw, bar, PACKED || !pp);
         save_ckpt(1 + s, x);
         if (alias) __syncthreads();
+        if constexpr (PACKED) bar();      // the group's loads are done before its row is written
         float* const prow0 =
             group_cs_bar ? reinterpret_cast<float*>(region + a.nlpr_off + (s & 1) * a.pbuf_bytes)
                          : prowA;
         {
-            float* prow = prow0 + gi * a.pstride;
+            float* prow = prow0 + gi * rs;
             const int mb = a.H + a.p_off;
             // With E = 16 the swizzle period is 64 floats: for NP/E a multiple of 64 every slot's
             // row index is base + (NP/E) t with one XOR constant, so the stores use immediate
-            // offsets; the halo (H <= NP/E) can only meet slots 0 and E - 1.
-            constexpr bool kFlat = (E == 16) && (TPF % 64 == 0);
-            const bool flat = kFlat && a.H <= TPF;
+            // offsets.  With E = 32 and NP/E = 32 the XOR term of slot t depends on t mod 4 only
+            // (see below).  Either way the halo (H <= NP/E) can only meet slots 0 and E - 1.
+            constexpr bool kFlat16 = (E == 16) && (TPF % 64 == 0);
+            constexpr bool kFlat32 = (E == 32) && (TPF == 32) && !PERPOL;
+            const bool flat = (kFlat16 || kFlat32) && a.H <= TPF;
             const int dstride = PERPOL ? a.n_sb * a.pstride : 0;     // D rows follow P rows
             // After the shuffle both lanes of an x/y pair hold |x|^2 + |y|^2 of every slot, so
             // lane p stores the slots t with t % 2 == p: one store instruction per two slots and
@@ -503,7 +538,18 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                 pw = p == 0 ? own0 + oth0 : oth1 + own1;
                 dv = p == 0 ? own0 - oth0 : oth1 - own1;
             };
-            if (flat) {
+            auto halo = [&](int t2, float pw, float dv) {
+                // the halo can only meet slot 0 (lane 0 at t2 = 0) and slot E - 1 (lane 1)
+                if (t2 == 0 && p == 0 && j < a.H) {
+                    prow[pswz<E>(mb + j + NP)] = pw;
+                    if constexpr (PERPOL) prow[pswz<E>(mb + j + NP) + dstride] = dv;
+                }
+                if (t2 == E - 2 && p == 1 && j + TPF * (E - 1) >= NP - a.H) {
+                    prow[pswz<E>(mb + j + TPF * (E - 1) - NP)] = pw;
+                    if constexpr (PERPOL) prow[pswz<E>(mb + j + TPF * (E - 1) - NP) + dstride] = dv;
+                }
+            };
+            if (kFlat16 && flat) {
                 float* const pbase = prow + pswz<E>(mb + j) + TPF * p;
 #pragma unroll
                 for (int t2 = 0; t2 < E; t2 += 2) {
@@ -511,15 +557,22 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                     slot_pair(t2, pw, dv);
                     pbase[TPF * t2] = pw;
                     if constexpr (PERPOL) pbase[TPF * t2 + dstride] = dv;
-                    // the halo can only meet slot 0 (lane 0 at t2 = 0) and slot E - 1 (lane 1)
-                    if (t2 == 0 && p == 0 && j < a.H) {
-                        prow[pswz<E>(mb + j + NP)] = pw;
-                        if constexpr (PERPOL) prow[pswz<E>(mb + j + NP) + dstride] = dv;
-                    }
-                    if (t2 == E - 2 && p == 1 && j + TPF * (E - 1) >= NP - a.H) {
-                        prow[pswz<E>(mb + j + TPF * (E - 1) - NP)] = pw;
-                        if constexpr (PERPOL) prow[pswz<E>(mb + j + TPF * (E - 1) - NP) + dstride] = dv;
-                    }
+                    halo(t2, pw, dv);
+                }
+            } else if (kFlat32 && flat) {
+                // pswz<32>(m), m = u + 32 t with u = mb + j: m >> 5 = (u >> 5) + t, and the XOR
+                // term (((u >> 5) + t) & 3) << 2 touches bits 2 and 3 only, so pswz(m) =
+                // (u ^ X(t mod 4)) + 32 t.  Lane p stores t = p mod 2, i.e. t mod 4 in {p, p + 2}:
+                // two bases per lane (32 p folded in), immediate offsets 32 t2.
+                const int u = mb + j;
+                float* const pb0 = prow + (u ^ ((((u >> 5) + p) & 3) << 2)) + 32 * p;
+                float* const pb2 = prow + (u ^ ((((u >> 5) + p + 2) & 3) << 2)) + 32 * p;
+#pragma unroll
+                for (int t2 = 0; t2 < E; t2 += 2) {
+                    float pw, dv;
+                    slot_pair(t2, pw, dv);
+                    ((t2 & 2) ? pb2 : pb0)[32 * t2] = pw;
+                    halo(t2, pw, dv);
                 }
             } else {
 #pragma unroll
@@ -543,31 +596,41 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                 }
             }
         }
+        if constexpr (PACKED) {
+#pragma unroll
+            for (int u = 0; u < kParkSlots; ++u) park[u * 2 * TPF] = x[E - kParkSlots + u];
+        }
         if (a.taps_smem) cp_async_wait_all();
         __syncthreads();
 #pragma unroll
         for (int h8 = 0; h8 < E / 16; ++h8)
-            nlpr_rotation8<E, PERPOL>(a, prow0, cs_row, s_rot, taps_buf, s, gi,
-                              E * j + (E / 2) * p + 8 * h8);
+            nlpr_rotation8<E, PERPOL, CSH>(a, prow0, rs, cs_row, s_rot, taps_buf, s, gi,
+                                           E * j + (E / 2) * p + 8 * h8);
         // (cos, sin) of subband gi are written and read by group gi only.  With two intensity
         // buffers nothing else is shared before the next step's intensity barrier: a group that
-        // runs ahead writes the other buffer.
+        // runs ahead writes the other buffer.  The packed layout needs the block barrier: every
+        // group reads every intensity row, and the next exchange overwrites them.
         if (group_cs_bar) {
             bar();
         } else {
             __syncthreads();
         }
+        if constexpr (PACKED) {
+#pragma unroll
+            for (int u = 0; u < kParkSlots; ++u) x[E - kParkSlots + u] = park[u * 2 * TPF];
+        }
 #pragma unroll
         for (int t = 0; t < E; ++t) {
-            const float2 r = (TPF >= 16) ? cs_row[cs_base + (TPF + TPF / 16) * t]
-                                         : cs_row[cpad(j + TPF * t)];
+            const float2 r = (TPF >= (1 << CSH)) ? cs_row[cs_base + (TPF + (TPF >> CSH)) * t]
+                                                 : cs_row[cpad(j + TPF * t)];
             // per-polarization form: r holds the two angles
             float2 rot = r;
             if constexpr (PERPOL) rot = rotation_factor(p == 0 ? r.x : r.y, s_rot);
             x[t] = c_mul(x[t], rot);
         }
         if (alias) __syncthreads();
-        fft_regs<NP, E, false, true>(x, j, fwd1, fwd2, s_tw, bar, !pp);  // back to subband bins
+        if constexpr (PACKED) bar();      // the group's (cos, sin) reads come before its stores
+        fft_regs<NP, E, false, true>(x, j, fwd1, fwd2, s_tw, bar, !PACKED && !pp);
         gvd_apply<NP, E>(x, s < a.n_st - 1 ? a.gvd_half + half_len : a.gvd_last, j, ci);
     }
 
@@ -582,13 +645,13 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
             const int kap = j + TPF * t;
             int K = ci + (kap < NP / 2 ? kap : kap - NP);
             if (K < 0) K += N;
-            ex[2 * xpad(K)] = x[t];
+            ex[2 * xpad_s<SH>(K)] = x[t];
         }
         __syncthreads();
         // Z_r[kap] = sum_q conj(W_N^(K r)) Xi[K], K = kap + NP q (q outermost, as above), with
         // W_N^(K r) = W_N^((j + NP q) r) W_N^((N'/E) t r): one table load per q and thread
         const float2* wr = a.mix_tw + (size_t)gi * N;
-        const float2* tm = a.mix_tw + (size_t)a.n_sb * (N + E) + gi * E;   // [n_sb][E], row gi
+        const float2* tm = a.mix_tm + gi * E;                      // [n_sb][E], row gi
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
         for (int q = 0; q < a.n_sb; ++q) {
@@ -596,14 +659,30 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int K = j + TPF * t + NP * q;
-                const float2 w = E == 16 ? c_mul(w0, __ldg(tm + t)) : __ldg(wr + K);   // as above
-                x[t] = c_add(x[t], c_mulc(ex[2 * xpad(K)], w));
+                const float2 w = kFactor ? c_mul(w0, __ldg(tm + t)) : __ldg(wr + K);   // as above
+                x[t] = c_add(x[t], c_mulc(ex[2 * xpad_s<SH>(K)], w));
             }
         }
     }
     __syncthreads();
     fft_regs<NP, E, true, true>(x, j, e, s_tw, bar);               // x[n_sb n' + r], r = gi
-    if (real) {
+    if constexpr (PACKED) {
+        // Through shared memory in sample order, then coalesced stores: consecutive threads write
+        // consecutive samples (16 bytes each in complex64, 8 bytes in 16-bit storage).
+        __syncthreads();                                           // every exchange load is done
+        Pol* st = reinterpret_cast<Pol*>(region);
+#pragma unroll
+        for (int t = 0; t < E; ++t) st[2 * (a.n_sb * (j + TPF * t) + gi) + p] = S::from_f32(x[t]);
+        __syncthreads();
+        if (real) {
+            using Smp = typename std::conditional<ST == 0, float4, uint2>::type;
+            const long long base = (long long)blk * a.V;           // first kept sample
+            const int nv = (int)min((long long)a.V, a.L - base);
+            const Smp* src = reinterpret_cast<const Smp*>(region) + a.n_ov / 2;
+            Smp* dst = reinterpret_cast<Smp*>(a.out) + (long long)seq * a.L + base;
+            for (int n = rem; n < nv; n += TB) dst[n] = src[n];
+        }
+    } else if (real) {
         Pol* dst = reinterpret_cast<Pol*>(a.out) + 2 * (long long)seq * a.L + p;
         const int lo = a.n_ov / 2;
         const long long base = (long long)blk * a.V - lo;
@@ -622,16 +701,18 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 // One launch over `a.batch` sequences of one plan: CTA b runs blocks b G .. b G + G - 1 of the
 // flattened (sequence, block) list.
 template <int NP, int ST, bool PERPOL = false>
-__global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) {
+__global__ void __launch_bounds__(chain_max_threads(NP, PERPOL), chain_min_ctas(NP, PERPOL))
+    cbessfm_fwd_kernel(const ChainArgs a) {
+    constexpr int E = chain_slots(NP, PERPOL);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kMaxG];
     __shared__ float2 s_rot[kRotTable];
-    const ThreadPos tp = thread_pos<NP>(a.n_sb);
+    const ThreadPos tp = thread_pos<NP, E>(a.n_sb);
     float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)a.G * a.region_bytes);
     float4* const s_taps = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_tw) +
-                                                     chain_tw_bytes(fft_tw_size(NP)));
+                                                     chain_tw_bytes(fft_tw_size(NP, E)));
     for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
-    for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(a.fft_tw + k);
+    for (int k = tp.tid; k < fft_tw_size(NP, E); k += blockDim.x) s_tw[k] = __ldg(a.fft_tw + k);
     if (tp.tid < a.G) mbar_init(&bars[tp.tid], 1);
     mbar_fence_init();
     __syncthreads();
@@ -646,16 +727,18 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_kernel(const ChainArgs a) 
 
 // Forward launch that also writes the adjoint's checkpoints (complex64 storage).
 template <int NP>
-__global__ void __launch_bounds__(640, 1) cbessfm_fwd_ckpt_kernel(const ChainArgs a) {
+__global__ void __launch_bounds__(chain_max_threads(NP, false), chain_min_ctas(NP, false))
+    cbessfm_fwd_ckpt_kernel(const ChainArgs a) {
+    constexpr int E = chain_slots(NP, false);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kMaxG];
     __shared__ float2 s_rot[kRotTable];
-    const ThreadPos tp = thread_pos<NP>(a.n_sb);
+    const ThreadPos tp = thread_pos<NP, E>(a.n_sb);
     float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)a.G * a.region_bytes);
     float4* const s_taps = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_tw) +
-                                                     chain_tw_bytes(fft_tw_size(NP)));
+                                                     chain_tw_bytes(fft_tw_size(NP, E)));
     for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
-    for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(a.fft_tw + k);
+    for (int k = tp.tid; k < fft_tw_size(NP, E); k += blockDim.x) s_tw[k] = __ldg(a.fft_tw + k);
     if (tp.tid < a.G) mbar_init(&bars[tp.tid], 1);
     mbar_fence_init();
     __syncthreads();
@@ -673,21 +756,24 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_ckpt_kernel(const ChainArg
 // decreasing cost on the host) until the list is exhausted.  Each item runs G consecutive blocks
 // of one job; per-job parameters come from `jobs`.
 template <int NP, int ST, bool PERPOL = false>
-__global__ void __launch_bounds__(640, 1) cbessfm_fwd_persistent_kernel(
-    const ChainArgs* __restrict__ jobs, const int2* __restrict__ items, int n_items,
-    unsigned int* __restrict__ counter, int n_sb, int G, int region_bytes) {
+__global__ void __launch_bounds__(chain_max_threads(NP, PERPOL), chain_min_ctas(NP, PERPOL))
+    cbessfm_fwd_persistent_kernel(const ChainArgs* __restrict__ jobs,
+                                  const int2* __restrict__ items, int n_items,
+                                  unsigned int* __restrict__ counter, int n_sb, int G,
+                                  int region_bytes) {
+    constexpr int E = chain_slots(NP, PERPOL);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kMaxG];
     __shared__ float2 s_rot[kRotTable];
     __shared__ ChainArgs s_job;
     __shared__ int s_item;
-    const ThreadPos tp = thread_pos<NP>(n_sb);
+    const ThreadPos tp = thread_pos<NP, E>(n_sb);
     float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)G * region_bytes);
     float4* const s_taps = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_tw) +
-                                                     chain_tw_bytes(fft_tw_size(NP)));
-    {   // every job of the launch has this N', so any job's twiddle table will do
+                                                     chain_tw_bytes(fft_tw_size(NP, E)));
+    {   // every job of the launch has this N' and form, so any job's twiddle table will do
         const float2* tw = jobs[items[0].x].fft_tw;
-        for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(tw + k);
+        for (int k = tp.tid; k < fft_tw_size(NP, E); k += blockDim.x) s_tw[k] = __ldg(tw + k);
     }
     if (tp.tid < G) mbar_init(&bars[tp.tid], 1);
     mbar_fence_init();
@@ -739,9 +825,16 @@ template <int NP, int ST>
 cudaError_t fwd_prepare(int smem_bytes) {
     cudaError_t e = cudaFuncSetAttribute(cbessfm_fwd_kernel<NP, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    // the packed layout runs two CTAs per SM: ask for the whole shared-memory carve-out
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cbessfm_fwd_kernel<NP, ST>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(cbessfm_fwd_persistent_kernel<NP, ST>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(cbessfm_fwd_persistent_kernel<NP, ST>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if constexpr (ST == 0) {
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(cbessfm_fwd_kernel<NP, 0, true>,

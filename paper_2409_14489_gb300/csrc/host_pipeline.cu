@@ -19,6 +19,7 @@
 
 #include "abi_guard.h"
 #include "block_count.h"
+#include "device_common.cuh"
 #include "internal.h"
 
 namespace cbessfm {
@@ -108,7 +109,10 @@ static cbessfm_status backpropagate_host_body(cbessfm_plan* plan, const void* ho
     std::lock_guard<std::mutex> call_lock(hp.mu);
     // CTAs per launch: one wave of resident CTAs unless the caller fixes the blocks per launch
     // (rounded up to whole CTAs of G blocks)
-    int wave = hp.n_sm * (resident_blocks(p.G, p.threads / p.G, p.region_bytes, p.tbl_bytes) / p.G);
+    int wave = hp.n_sm * (resident_blocks(p.G, p.threads / p.G, p.region_bytes, p.tbl_bytes,
+                                          chain_max_threads(p.n_fft, p.per_pol != 0),
+                                          chain_min_ctas(p.n_fft, p.per_pol != 0)) /
+                          p.G);
     if (wave < 1) wave = 1;
     // automatic sizing: one wave first (it waits only for the copies of the blocks it reads),
     // then two waves per launch (fewer launch boundaries, each of which drains the GPU; on the

@@ -16,9 +16,21 @@ namespace cbessfm {
 //                   before a store), the (cos, sin) rows inside the array the inverse FFT read
 //                   last, then one or two intensity-row buffers.  With two buffers (pbuf_bytes >
 //                   0) the barrier after the FIR covers only the subband group.
+//  kLayoutPacked:   the two-pass plan's layout (N' = 1024, 32 slots): one exchange array per
+//                   subband group, holding the group's intensity row (at its start) and its
+//                   (cos, sin) row (after it) while the FFTs do not use it.
 constexpr int kLayoutAlias = 0;
 constexpr int kLayoutSeparate = 1;
 constexpr int kLayoutPingPong = 2;
+constexpr int kLayoutPacked = 3;
+// Packed layout: complex slots per thread parked in shared memory during the FIR (the registers
+// they free keep the FIR's window and accumulators out of local memory), after the group's
+// (cos, sin) row: [kParkSlots][2 NP/E] complex.
+constexpr int kParkSlots = 8;
+
+// Default bound of the chain kernels' waits for their staging copies, in SM clock cycles
+// (about 2 s at 2 GHz: never reached by a live copy).
+constexpr long long kWaitCycles = 4000000000LL;
 
 // Kernel arguments of the chain kernels (forward and adjoint share them).
 struct ChainArgs {
@@ -45,9 +57,10 @@ struct ChainArgs {
                                  // unit factor (x 1/N) as kind 3
     const float2* gvd_first;     // gvd_half kind of the first GVD (kind 0, or 3 in later passes)
     const float2* gvd_last;      // gvd_half kind of the last step's GVD (kind 2, or 1)
-    const float2* mix_tw;        // [n_sb][N]: W_N^(K r), then [n_sb][E] DEMUX and [n_sb][E] MUX
-                                 // slot factors (see the chain's DEMUX and MUX)
-    const float2* fft_tw;        // FFT pass twiddles (fft_tw_size(NP))
+    const float2* mix_tw;        // [n_sb][N]: W_N^(K r)
+    const float2* mix_td;        // [n_sb][E] DEMUX slot factors of the kernel's E (see the
+    const float2* mix_tm;        // [n_sb][E] MUX slot factors      chain's DEMUX and MUX)
+    const float2* fft_tw;        // FFT pass twiddles of the kernel's plan (fft_tw_size(NP, E))
     const float* taps;           // [n_st][n_sb][n_sb][ntaps_pad]
     const float2* rot_tbl;       // [256] exp(j 2 pi k / 256)
     unsigned int* status;        // device status word
@@ -59,6 +72,8 @@ struct ChainArgs {
     float2* stash;               // adjoint: per-block scratch, two fields [2][gi][idx][p]
     int want_ratio;              // adjoint: 1 if dL/drho is requested
     float kd0;                   // adjoint: 2 pi^2 beta2 L_step (R/N)^2 (ratio-gradient weights)
+    long long wait_cycles;       // bound of the waits for the staging copies (SM cycles; <= 0:
+                                 // one non-blocking test)
     int cta0, n_ctas;            // forward launch over CTAs [cta0, cta0 + n_ctas) of the whole
                                  // batch's grid (n_ctas = 0: to the end); CTA c runs work items
                                  // c G .. c G + G - 1, item = seq * n_blocks + blk
@@ -77,8 +92,12 @@ struct PlanImpl {
     double step_length = 0.0;
     float2* d_gvd = nullptr;      // [3][n_sb][NP]
     float2* d_gvd_half = nullptr; // [4][N/2 + 1]
-    float2* d_mix_tw = nullptr;   // [n_sb][N] + 2 [n_sb][E]
-    float2* d_fft_tw = nullptr;
+    float2* d_mix_tw = nullptr;   // [n_sb][N], then DEMUX and MUX slot factors [n_sb][E] of the
+                                  // Manakov forward chain's E, then of fft_slots (classic)
+    float2* d_fft_tw = nullptr;   // FFT twiddles of the Manakov forward chain's plan
+    float2* d_fft_tw_cl = nullptr;// FFT twiddles of the fft_slots plan (adjoint, per-polarization
+                                  // chain); the same table when both plans agree
+    long long wait_cycles = kWaitCycles;
     float* d_taps = nullptr;      // [n_st][n_sb][n_sb][ntaps_pad]
     float2* d_rot = nullptr;      // [256] exp(j 2 pi k / 256) from FP64
     float* d_taps_t = nullptr;    // transposed, reversed taps for the adjoint's intensity gradient
@@ -97,14 +116,19 @@ cudaError_t launch_forward(const PlanImpl& p, const ChainArgs& a, cudaStream_t s
 cudaError_t prepare_forward(int np, int storage, int smem_bytes);
 
 ChainArgs make_chain_args(const PlanImpl& p);
+// The tables of the fft_slots (classic) plan: FFT twiddles and DEMUX/MUX slot factors, for the
+// adjoint kernel and the per-polarization chain.
+void classic_tables(const PlanImpl& p, ChainArgs& a);
 
 // Launch-shape limits shared by the plan and batch builders.
 constexpr int kMaxDynSmem = 224 * 1024;     // 227 KB per block minus room for static shared memory
 constexpr int kMaxThreads = 640;
 constexpr int kMaxG = 16;
 // OLS blocks per CTA for a block of `tb` threads and `region_bytes` of shared memory, with
-// `extra_bytes` more per CTA (0 = none fits).
-int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands, int extra_bytes = 0);
+// `extra_bytes` more per CTA, in a kernel compiled for at most `max_threads` threads and at
+// least `min_ctas` CTAs per SM (0 = none fits).
+int choose_blocks_per_cta(int tb, int region_bytes, int tpf, int bands, int extra_bytes = 0,
+                          int max_threads = kMaxThreads, int min_ctas = 1);
 
 // Per-CTA shared tables of the forward chain, after the G block regions: the FFT pass twiddles of
 // N' (rounded to 128 bytes), then, when taps are staged, two buffers of one step's taps
@@ -124,8 +148,10 @@ const char* last_error_text();
 const PlanImpl* plan_impl(const cbessfm_plan* plan);
 
 // OLS blocks resident per SM for G blocks of `tb` threads per CTA, `region` bytes each, and
-// `tables` bytes of per-CTA tables.
-int resident_blocks(int G, int tb, int region, int tables);
+// `tables` bytes of per-CTA tables, in a kernel compiled for `max_threads` threads and
+// `min_ctas` CTAs per SM (which fixes its registers per thread).
+int resident_blocks(int G, int tb, int region, int tables, int max_threads = kMaxThreads,
+                    int min_ctas = 1);
 
 // cbessfm_backpropagate restricted to the CTAs [cta0, cta0 + n_ctas) of the whole batch's grid
 // (n_ctas = 0: to the end), i.e. the work items [cta0 G, (cta0 + n_ctas) G) of the flattened

@@ -29,7 +29,7 @@ namespace cbessfm {
 namespace {
 
 constexpr int kNoallocMaxJobs = 64;
-constexpr int kDescBytes = 256;
+constexpr int kDescBytes = 320;
 constexpr int kCounterOff = 0;
 constexpr int kDescOff = 256;
 constexpr int kPrefixOff = kDescOff + kNoallocMaxJobs * kDescBytes;
@@ -43,7 +43,8 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 // prefix sums: item i belongs to the job k with prefix[k] <= i < prefix[k + 1] and covers blocks
 // (i - prefix[k]) G .. + G - 1 of that job.  Jobs are ordered by decreasing cost on the host.
 template <int NP>
-__global__ void __launch_bounds__(640, 1) cbessfm_fwd_noalloc_kernel(
+__global__ void __launch_bounds__(chain_max_threads(NP, false), chain_min_ctas(NP, false))
+    cbessfm_fwd_noalloc_kernel(
     const ChainArgs* __restrict__ jobs, const int* __restrict__ prefix, int njobs,
     unsigned int* __restrict__ counter, int n_sb, int G, int region_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -51,11 +52,12 @@ __global__ void __launch_bounds__(640, 1) cbessfm_fwd_noalloc_kernel(
     __shared__ float2 s_rot[kRotTable];
     __shared__ ChainArgs s_job;
     __shared__ int s_item;
-    const ThreadPos tp = thread_pos<NP>(n_sb);
+    constexpr int E = chain_slots(NP, false);
+    const ThreadPos tp = thread_pos<NP, E>(n_sb);
     float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)G * region_bytes);
     float4* const s_taps = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_tw) +
-                                                     chain_tw_bytes(fft_tw_size(NP)));
-    for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(jobs[0].fft_tw + k);
+                                                     chain_tw_bytes(fft_tw_size(NP, E)));
+    for (int k = tp.tid; k < fft_tw_size(NP, E); k += blockDim.x) s_tw[k] = __ldg(jobs[0].fft_tw + k);
     if (tp.tid < G) mbar_init(&bars[tp.tid], 1);
     mbar_fence_init();
     const int n_items = prefix[njobs];
@@ -216,15 +218,17 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
         any_taps = any_taps || desc[k].taps_smem;
         order[k] = k;
     }
-    const int tpf = np / fft_slots(np);
+    const int E = chain_slots(np, false);
+    const int tpf = np / E;
     const int tb = 2 * n_sb * tpf;
+    const int max_threads = chain_max_threads(np, false), min_ctas = chain_min_ctas(np, false);
     // per-CTA tables after the block regions: twiddles, plus tap buffers when they fit
-    const int tw = chain_tw_bytes(fft_tw_size(np));
+    const int tw = chain_tw_bytes(fft_tw_size(np, E));
     int tbl = tw + (any_taps ? chain_taps_bytes(n_sb) : 0);
-    int G = choose_blocks_per_cta(tb, region, tpf, n_sb, tbl);
+    int G = choose_blocks_per_cta(tb, region, tpf, n_sb, tbl, max_threads, min_ctas);
     if (G < 1 && any_taps) {
         tbl = tw;
-        G = choose_blocks_per_cta(tb, region, tpf, n_sb, tbl);
+        G = choose_blocks_per_cta(tb, region, tpf, n_sb, tbl, max_threads, min_ctas);
     }
     if (G < 1) return fail(CBESSFM_ERR_UNSUPPORTED, "no CTA shape for n_fft %d, bands %d", np, n_sb);
     // longest processing time first: order jobs by decreasing cost per work item (insertion
