@@ -36,7 +36,7 @@ from paper_2409_14489_gb300 import cost  # noqa: E402
 WORKLOAD = "c2_wdm15"
 METRIC = "DBP 2D symbols/s on 1 GB300 (plain vs batched/adjoint) at ≤1e-5 rel. err; % HBM roofline"
 UNIT = "2D symbols/s"
-N_SM, FP32_LANES = 152, 128
+FP32_LANES = 128          # FP32 FMA lanes per SM (sm_100 family); the SM count comes from the device
 FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
 KERNEL_SOURCES = ["paper_2409_14489_gb300/csrc/fwd_kernel.cuh",
                   "paper_2409_14489_gb300/csrc/device_common.cuh",
@@ -270,7 +270,10 @@ def form_adjoint(steps: int, warmup: int):
             "value": sym2d / (t / 1e3), "unit": UNIT, "ms_per_step": t, "sym2d_per_step": sym2d,
             "forward_only_ms": t_fwd, "taps_only_gradient_ms": t_taps,
             "workspace_bytes": int(ws.numel()),
-            "gpu_launches_per_step": 4}
+            "gpu_launches_per_step": 4,
+            # the paper counts no adjoint; its count for the chain and for the transposed chain of
+            # the backward pass, 2 x the forward flops of this workload
+            "algorithmic_flops": 2.0 * flops_per_2d(wl) * sym2d}
 
 
 def form_precision(plan_c64, taps, x_c64, steps: int, warmup: int):
@@ -546,10 +549,18 @@ def run_gpu(args, wl, taps):
     e2e_ms = timed(e2e_step)
     e2e_seq_ms = timed(e2e_step_sequential)
 
+    # measured FP32 FMA rate of this device (the ALU roof), with the clocks sampled meanwhile
+    peak_sampler = ClockSampler(local)
+    fp32_meas, n_sm = cbessfm.measure_fp32_peak(1000)   # about half a second
+    peak_clocks = peak_sampler.stop()
+    n_sm_dev = torch.cuda.get_device_properties(local).multi_processor_count
+
     if rank == 0:
         pk, pk_kind = peaks()
-        sm_mhz = float(pk.get("sm_max_mhz", FALLBACK["sm_max_mhz"]))
-        fp32_peak = N_SM * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s
+        sm_mhz = float((clocks or {}).get("sm_max_mhz") or
+                       pk.get("sm_max_mhz", FALLBACK["sm_max_mhz"]))
+        fp32_derived = n_sm_dev * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12   # TFLOP/s
+        fp32_peak = fp32_meas / 1e12                                     # measured, TFLOP/s
         avg_s = total_ms / args.steps / 1e3
         flops_launch = flops_per_2d(wl) * sym_per_step
         achieved = flops_launch / avg_s / 1e12
@@ -567,6 +578,11 @@ def run_gpu(args, wl, taps):
             forms["adjoint"] = form_adjoint(max(3, min(args.steps, 10)), 2)
         except Exception as exc:
             forms["adjoint"] = {"error": repr(exc)}
+        if "algorithmic_flops" in forms["adjoint"]:
+            ad = forms["adjoint"]
+            ad["algorithmic_tflops"] = ad["algorithmic_flops"] / (ad["ms_per_step"] / 1e3) / 1e12
+            ad["frac_of_fp32_peak"] = ad["algorithmic_tflops"] / fp32_peak
+            ad["x_forward"] = ad["ms_per_step"] / ad["forward_only_ms"]
         try:
             forms["precision"] = form_precision(plan, taps, x, max(3, min(args.steps, 10)), 2)
         except Exception as exc:
@@ -606,8 +622,14 @@ def run_gpu(args, wl, taps):
                 "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak, "traffic": recorded_traffic(),
                 "ncu": recorded_ncu_counters(),
-                "peak_source": (f"FP32: {N_SM} SMs x {FP32_LANES} lanes x 2 flop x "
-                                f"{sm_mhz:g} MHz ({pk_kind} max SM clock)"),
+                "peak_source": ("measured: cbessfm_measure_fp32_peak, independent FFMA chains "
+                                f"on all {n_sm} SMs, fastest of 1000 launches (CUDA events)"),
+                "peak_clocks": peak_clocks,
+                "sm_count": n_sm_dev,
+                "derived_peak": fp32_derived,
+                "derived_peak_source": (f"{n_sm_dev} SMs (device) x {FP32_LANES} lanes x 2 flop x "
+                                        f"{sm_mhz:g} MHz (max SM clock)"),
+                "frac_of_derived": achieved / fp32_derived,
                 "flops_per_launch": flops_launch,
                 "flops_model": "paper RM + RA per 2D symbol (Eq. (costRM) and its RA companion)",
                 "hbm": {"bytes_per_launch": bytes_launch,

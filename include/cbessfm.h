@@ -313,6 +313,19 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
 cbessfm_status cbessfm_set_nlpr_mode(cbessfm_plan* plan, int per_polarization);
 
 /*
+ * cbessfm_set_wait_limit -- bound of the forward chain kernels' waits for the bulk copies (TMA)
+ * that stage each overlap-and-save block into shared memory, in SM clock cycles.  No part of the
+ * paper: a guard against a copy that never completes.  cycles > 0: the bound; 0: one
+ * non-blocking test per wait; < 0: the default (4e9 cycles, about 2 s, never reached by a live
+ * copy).  A wait that runs out sets bit 0 of the plan's status word (cbessfm_get_status then
+ * returns CBESSFM_ERR_TIMEOUT); the CTA then waits, with the default bound, for its copies in
+ * flight to land and returns without writing its blocks' output.  Applies to launches made
+ * after the call (plain, host-pipelined, streamed, checkpointed, and batches created after it).
+ * Synchronous with respect to the host; CBESSFM_ERR_INVALID_ARG for a NULL plan.
+ */
+cbessfm_status cbessfm_set_wait_limit(cbessfm_plan* plan, long long cycles);
+
+/*
  * cbessfm_get_status -- synchronize `stream`, then read and clear the plan's device status word
  * (bit 0: a bounded wait for a shared-memory copy gave up -> CBESSFM_ERR_TIMEOUT).
  */

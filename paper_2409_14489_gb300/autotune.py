@@ -128,7 +128,8 @@ class Autotuner:
             plan = cbessfm.Plan(link, shape.n_sb, shape.n_st, 0.5, taps, nf, ov,
                                 storage=shape.storage)
             V = plan.valid
-            L = 8 * 152 * V                           # enough blocks to fill the GPU
+            n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+            L = 8 * n_sm * V                          # enough blocks to fill the GPU
             if shape.storage == 0:
                 x = torch.zeros(L, 2, dtype=torch.complex64, device="cuda")
             else:

@@ -96,6 +96,8 @@ def _load():
     lib.cbessfm_backpropagate_host.argtypes = [P, c_void_p, c_void_p, c_void_p, c_void_p,
                                                c_int64, c_int, c_int, c_void_p]
     lib.cbessfm_backpropagate_host.restype = c_int
+    lib.cbessfm_set_wait_limit.argtypes = [P, ctypes.c_longlong]
+    lib.cbessfm_set_wait_limit.restype = c_int
     lib.cbessfm_set_nlpr_mode.argtypes = [P, c_int]
     lib.cbessfm_set_nlpr_mode.restype = c_int
     lib.cbessfm_analytic_taps.argtypes = [ctypes.POINTER(LinkStruct), c_int, c_int, c_int,
@@ -355,6 +357,11 @@ class Plan:
     def set_ratio(self, ratio: float, stream=None):
         _check(_lib.cbessfm_set_ratio(self._h, float(ratio), _stream_handle(stream)))
         self.ratio = float(ratio)
+
+    def set_wait_limit(self, cycles: int):
+        """Bound of the staging waits in SM cycles (``cbessfm_set_wait_limit``): > 0 the bound,
+        0 one non-blocking test, < 0 the default."""
+        _check(_lib.cbessfm_set_wait_limit(self._h, int(cycles)))
 
     def status(self, stream=None) -> int:
         """Synchronize and return the device status as a cbessfm_status value (0 = OK)."""

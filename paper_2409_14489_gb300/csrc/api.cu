@@ -151,9 +151,9 @@ bool choose_layout(PlanImpl& p, int tb, int tpf) {
     if (chain_packed(n_fft, per_pol)) {
         // one exchange array per group; its intensity row, (cos, sin) row (one spare per 32) and
         // the parked slots fit inside it
-        const int xl_bytes = 16 * xpad_len_s(n_fft, fft_xsh(n_fft, E));
-        if (4 * p.pstride + 8 * (n_fft + n_fft / 32) + 8 * kParkSlots * 2 * tpf > xl_bytes)
-            return false;
+        // the array grows past its exchange size when long filters need longer intensity rows
+        const int rows_bytes = 4 * p.pstride + 8 * (n_fft + n_fft / 32) + 8 * kParkSlots * 2 * tpf;
+        const int xl_bytes = round_up(std::max(16 * xpad_len_s(n_fft, fft_xsh(n_fft, E)), rows_bytes), 128);
         const int region = round_up(bands * xl_bytes, 128);
         int tbl = tw_taps;
         int G = choose_blocks_per_cta(tb, region, tpf, bands, tbl, max_threads, min_ctas);
@@ -633,6 +633,13 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
         const cudaError_t e = launch_forward(p, a, st);
         if (e != cudaSuccess) return cuda_fail(e, "streamed pass launch");
     }
+    return CBESSFM_OK;
+}
+
+extern "C" cbessfm_status cbessfm_set_wait_limit(cbessfm_plan* plan, long long cycles) {
+    clear_error();
+    if (!plan) return fail(CBESSFM_ERR_INVALID_ARG, "set_wait_limit: NULL plan");
+    plan->impl.wait_cycles = cycles < 0 ? kWaitCycles : cycles;
     return CBESSFM_OK;
 }
 

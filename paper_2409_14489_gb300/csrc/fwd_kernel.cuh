@@ -322,7 +322,10 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     constexpr bool kFactor = E == 16;
     const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
     unsigned char* region = smem + (size_t)g * region_bytes;
-    float2* const grpA = reinterpret_cast<float2*>(region) + gi * XL;   // this group's array A
+    // packed layout: the group arrays lie region_bytes / n_sb apart (at least XL float2; more when
+    // long filters need longer intensity rows than XL leaves room for)
+    const int XLg = PACKED ? region_bytes / (8 * a.n_sb) : XL;
+    float2* const grpA = reinterpret_cast<float2*>(region) + gi * XLg;  // this group's array A
     float2* e = grpA + p;
     const GroupBar<NP, E> bar{1 + g * a.n_sb + gi};
     // Ping-pong layout: a second exchange array B.  Three-pass FFTs exchange through A then B;
@@ -460,7 +463,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 #pragma unroll
         for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
         for (int r = 0; r < a.n_sb; ++r) {
-            const float2* er = eb + r * XL;
+            const float2* er = eb + r * XLg;
             const float2 w0 = __ldg(a.mix_tw + (size_t)r * N + K0);        // W_N^(K_0 r)
 #pragma unroll
             for (int t = 0; t < E; ++t) {
@@ -480,12 +483,12 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     gvd_apply<NP, E>(x, a.gvd_first, j, ci);                       // first GVD (x 1/N)
     save_ckpt(0, x);
     // intensity rows and (cos, sin) rows: see the kLayout* constants.  Packed layout: the row of
-    // subband l at the start of exchange array l (rows 2 XL floats apart), the group's (cos, sin)
+    // subband l at the start of exchange array l (rows 2 XLg floats apart), the group's (cos, sin)
     // row right after its own intensity row.
     const bool alias = !PACKED && a.layout == kLayoutAlias;
     float* const prowA = PACKED ? reinterpret_cast<float*>(region)
                                 : reinterpret_cast<float*>(region + a.nlpr_off);
-    const int rs = PACKED ? 2 * XL : a.pstride;                    // floats between rows
+    const int rs = PACKED ? 2 * XLg : a.pstride;                   // floats between rows
     float2* const cs_row =
         PACKED ? reinterpret_cast<float2*>(reinterpret_cast<float*>(grpA) + a.pstride)
         : pp   ? (NPASS > 2 ? grpB : grpA)

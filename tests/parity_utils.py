@@ -102,3 +102,28 @@ def rel_l2(a: np.ndarray, b: np.ndarray, name: str = "") -> float:
         with open(log, "a") as f:
             f.write(json.dumps({"case": name, "rel_l2": err}) + "\n")
     return err
+
+
+# Per-sample bound beside the relative L2 error: a defect confined to a few samples (one block
+# edge, one subband) moves the L2 norm little but shows in the largest sample error.  Every
+# sample's error must stay within PEAK_FACTOR x tol of the oracle's RMS sample magnitude.
+PEAK_FACTOR = 10.0
+
+
+def peak_rel(a: np.ndarray, b: np.ndarray) -> float:
+    """max_k |a_k - b_k| / rms(b): the largest sample error against the RMS sample magnitude."""
+    d = np.abs(np.asarray(a) - np.asarray(b)).max()
+    return float(d / np.sqrt(np.mean(np.abs(np.asarray(b)) ** 2)))
+
+
+def assert_parity(got: np.ndarray, want: np.ndarray, tol: float, name: str = "") -> float:
+    """rel-L2 <= tol and every sample within PEAK_FACTOR * tol * rms(want); returns the rel-L2."""
+    err = rel_l2(got, want, name)
+    peak = peak_rel(got, want)
+    log = os.environ.get("CBESSFM_PARITY_LOG")
+    if log and name:
+        with open(log, "a") as f:
+            f.write(json.dumps({"case": name + "/peak", "peak_rel": peak}) + "\n")
+    assert err <= tol, (name, err, tol)
+    assert peak <= PEAK_FACTOR * tol, (name, "peak", peak, PEAK_FACTOR * tol)
+    return err

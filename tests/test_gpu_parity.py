@@ -14,7 +14,7 @@ from oracle import channel, dbp as odbp, evaluate
 from synth import configs, signals
 
 from parity_utils import (Case, random_field, case_taps, oracle_params, make_plan, run_gpu, rel_l2,
-                          quantize)
+                          quantize, assert_parity)
 
 pytestmark = pytest.mark.gpu
 
@@ -53,8 +53,34 @@ def test_forward_matches_oracle_small(case):
     for b in range(case.batch):
         want = odbp.dbp_mode_b(field[b].astype(np.complex64).astype(np.complex128), p,
                                case.n_fft, case.overlap)
-        err = rel_l2(got[b], want, f"small/{case}/b{b}")
-        assert err <= TOL, (b, err)
+        assert_parity(got[b], want, TOL, f"small/{case}/b{b}")
+    assert plan.status() == 0
+
+
+# Shapes at the edges of what plan_create accepts: more subbands (up to 16 at N' = 256, 10 at
+# 512) and long filters (up to N'/2 taps: the windowed FIR's general chunk loop and wide halos).
+# Taps scale as 1/ntaps so the nonlinear phase per step stays comparable.
+WIDE_CASES = [
+    Case(8, 256, 64, 2, 21, 0.3, 2 * 8 * 192 + 77, sample_rate=512e9, tap_scale=1.0 / 21),
+    Case(16, 256, 64, 2, 11, 0.3, 2 * 16 * 192 + 55, sample_rate=1024e9, tap_scale=1.0 / 11),
+    Case(10, 512, 128, 2, 45, 0.3, 2 * 10 * 384 + 333, sample_rate=640e9, tap_scale=1.0 / 45),
+    Case(5, 1024, 256, 2, 45, 0.3, 2 * 3840 + 555, sample_rate=640e9, tap_scale=1.0 / 45),
+    Case(2, 256, 64, 2, 127, 0.5, 3 * 384 + 11, sample_rate=128e9, tap_scale=1.0 / 127),
+    Case(3, 1024, 256, 1, 511, 0.5, 2 * 2304 + 99, sample_rate=192e9, tap_scale=1.0 / 511),
+    Case(5, 2048, 512, 1, 101, 0.3, 10240 + 4000, sample_rate=640e9, tap_scale=1.0 / 101),
+]
+
+
+@pytest.mark.parametrize("case", WIDE_CASES, ids=lambda c: f"sb{c.n_sb}_np{c.n_fft}_t{c.ntaps}")
+def test_forward_matches_oracle_wide_shapes(case):
+    taps = case_taps(case)
+    field = random_field(case)
+    plan = make_plan(case, taps)
+    got = run_gpu(plan, field)
+    p = oracle_params(case, taps.astype(np.float32).astype(np.float64))
+    want = odbp.dbp_mode_b(field[0].astype(np.complex64).astype(np.complex128), p, case.n_fft,
+                           case.overlap)
+    assert_parity(got[0], want, TOL, f"wide/{case}")
     assert plan.status() == 0
 
 
@@ -147,8 +173,7 @@ def test_c2_full_size_sampled_blocks():
         blocks = sorted({0, n_blocks - 1, int(rng.integers(1, n_blocks - 1))})
         want = odbp.dbp_mode_b(f32[b].astype(np.complex128), p, d.n_fft, d.overlap, blocks=blocks)
         sel = ~np.isnan(want[:, 0])
-        err = rel_l2(got[b][sel], want[sel], f"c2_full/realization{b}")
-        assert err <= TOL, (b, blocks, err)
+        assert_parity(got[b][sel], want[sel], TOL, f"c2_full/realization{b}")
     assert np.isfinite(got).all()
 
 
@@ -220,8 +245,7 @@ def test_reduced_precision_storage_matches_oracle(case):
     p = oracle_params(case, taps.astype(np.float32).astype(np.float64))
     for b in range(case.batch):
         want = odbp.dbp_mode_b(q_in[b], p, case.n_fft, case.overlap)
-        err = rel_l2(got[b], want, f"storage{case.storage}/{case}/b{b}")
-        assert err <= STORAGE_TOL[case.storage], (b, err)
+        assert_parity(got[b], want, STORAGE_TOL[case.storage], f"storage{case.storage}/{case}/b{b}")
 
 
 # Long-haul bound for the complex64 form.  The 1e-5 bound of the FP32 path holds on the plain
@@ -255,8 +279,7 @@ def test_c5_long_haul_sampled_blocks(storage, tol):
     nb = plan.n_blocks(case.L)
     want = odbp.dbp_mode_b(q_in, p, d.n_fft, d.overlap, blocks=[0, nb // 2, nb - 1])
     sel = ~np.isnan(want[:, 0])
-    err = rel_l2(got[sel], want[sel], f"c5_longhaul/storage{storage}")
-    assert err <= tol, err
+    assert_parity(got[sel], want[sel], tol, f"c5_longhaul/storage{storage}")
 
 
 @pytest.fixture(scope="module")

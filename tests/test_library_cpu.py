@@ -114,6 +114,8 @@ def test_every_entry_point_rejects_a_null_handle_without_a_device(lib):
         "streamed_workspace_size": lambda: L.cbessfm_streamed_workspace_size(
             P, 100, 1, ctypes.byref(size)),
         "get_status": lambda: L.cbessfm_get_status(P, P),
+        "set_wait_limit": lambda: L.cbessfm_set_wait_limit(P, 0),
+        "measure_fp32_peak": lambda: L.cbessfm_measure_fp32_peak(1, P, P, P),
     }
     for name, call in checks.items():
         st = call()
