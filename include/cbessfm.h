@@ -186,7 +186,8 @@ typedef struct cbessfm_batch cbessfm_batch;
 /*
  * cbessfm_batch_create -- validate the jobs, build and upload the work list.  Synchronous.
  * The batch owns its device descriptors (allocated here).  Job buffers are referenced, not
- * copied: run() processes whatever they hold at the time.
+ * copied: run() processes whatever they hold at the time.  Every job's plan must have been
+ * created on the current device, where the batch then runs (else CBESSFM_ERR_INVALID_ARG).
  */
 cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_batch** out);
 
@@ -211,15 +212,18 @@ cbessfm_status cbessfm_batch_destroy(cbessfm_batch* batch);
  * of cbessfm_batch_run, computing the same chain with the same per-block arithmetic.
  *   jobs, njobs  as for cbessfm_batch_create; 1 <= njobs <= 64, all jobs with the same n_fft and
  *                bands and complex64 storage (else CBESSFM_ERR_UNSUPPORTED with a message);
- *                in/out are the caller's device buffers.
- * The work list and counter live in one static device array of 17,152 bytes that every
+ *                in/out are the caller's device buffers; every job's plan must have been
+ *                created on the current device (else CBESSFM_ERR_INVALID_ARG).
+ * The work list and counter live in one static device array of 21,248 bytes that every
  * GPU loading the library holds until exit; nothing is allocated by the call.  The first call on
  * a device looks up that array's device address and sets the kernel's shared-memory limit, so
  * make the first call before any stream capture.  The descriptors are copied from host stack
- * memory with cudaMemcpyAsync, which waits for the stream's earlier work before returning.  All
+ * memory with cudaMemcpyAsync, so each call blocks the calling thread until the stream's
+ * earlier work has finished; a caller that must not wait uses cbessfm_batch_create / _run.  All
  * calls share the array and it keeps the last call's contents (the call clears the counter
  * itself): calls that overlap on the GPU, from two streams or two threads, race and must be
- * ordered by the caller.
+ * ordered by the caller.  A staging wait that runs out (cbessfm_set_wait_limit) is reported,
+ * as for cbessfm_batch_run, by cbessfm_get_status on the job's plan, not by this call's return.
  */
 cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int njobs,
                                          cbessfm_stream stream);

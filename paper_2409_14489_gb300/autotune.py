@@ -116,36 +116,42 @@ class Autotuner:
             pass
 
     def _measure(self, shape: JobShape, cands):
-        import numpy as np
-        import torch
-        from . import cbessfm
-        best, best_t = None, float("inf")
-        link = cbessfm.make_link(shape.beta2, shape.link_length, 1, shape.sample_rate)
-        taps = np.zeros((shape.n_st, shape.n_sb, shape.n_sb, shape.ntaps), np.float32)
-        if shape.n_st:
-            taps[..., shape.ntaps // 2] = 1.0
-        for nf, ov in cands:
-            plan = cbessfm.Plan(link, shape.n_sb, shape.n_st, 0.5, taps, nf, ov,
-                                storage=shape.storage)
-            V = plan.valid
-            n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-            L = 8 * n_sm * V                          # enough blocks to fill the GPU
-            if shape.storage == 0:
-                x = torch.zeros(L, 2, dtype=torch.complex64, device="cuda")
-            else:
-                dt = torch.float16 if shape.storage == 1 else torch.bfloat16
-                x = torch.zeros(L, 4, dtype=dt, device="cuda")
-            y = torch.empty_like(x)
-            for _ in range(2):
-                plan.backpropagate(x, y)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(3):
-                plan.backpropagate(x, y)
-            e1.record()
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / 3 / L                 # ms per valid sample
-            if t < best_t:
-                best, best_t = (nf, ov), t
-            plan.close()
-        return best
+        times = measure_candidates(shape, cands)
+        return min(times, key=times.get)
+
+
+def measure_candidates(shape: JobShape, cands=None, reps: int = 3) -> Dict[Tuple[int, int], float]:
+    """Time per valid sample (ms) of one plain launch of each candidate (N', N'_ov) on a zero
+    block sequence long enough to fill the GPU (8 blocks per SM), median-free mean of ``reps``
+    launches after two warm-ups."""
+    import numpy as np
+    import torch
+    from . import cbessfm
+    cands = candidates(shape) if cands is None else cands
+    link = cbessfm.make_link(shape.beta2, shape.link_length, 1, shape.sample_rate)
+    taps = np.zeros((shape.n_st, shape.n_sb, shape.n_sb, shape.ntaps), np.float32)
+    if shape.n_st:
+        taps[..., shape.ntaps // 2] = 1.0
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = {}
+    for nf, ov in cands:
+        plan = cbessfm.Plan(link, shape.n_sb, shape.n_st, 0.5, taps, nf, ov, storage=shape.storage)
+        V = plan.valid
+        L = 8 * n_sm * V                              # enough blocks to fill the GPU
+        if shape.storage == 0:
+            x = torch.zeros(L, 2, dtype=torch.complex64, device="cuda")
+        else:
+            dt = torch.float16 if shape.storage == 1 else torch.bfloat16
+            x = torch.zeros(L, 4, dtype=dt, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(2):
+            plan.backpropagate(x, y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            plan.backpropagate(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        out[(nf, ov)] = e0.elapsed_time(e1) / reps / L                # ms per valid sample
+        plan.close()
+    return out

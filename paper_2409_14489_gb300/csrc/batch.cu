@@ -59,10 +59,18 @@ static cbessfm_status batch_create_body(const cbessfm_job* jobs, int njobs, cbes
 
     std::vector<ChainArgs> args(njobs);
     std::map<std::tuple<int, int, int, int>, std::vector<int>> by_shape;
+    int dev = 0;
+    cudaError_t e = cudaSuccess;
     for (int k = 0; k < njobs; ++k) {
         const cbessfm_job& jb = jobs[k];
         const PlanImpl* p = plan_impl(jb.plan);
         if (p == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "job %d: plan is NULL", k);
+        // every plan's tables must be on the current device, where the batch's launches run
+        if (k == 0 && (e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        if (p->device != dev)
+            return fail(CBESSFM_ERR_INVALID_ARG,
+                        "job %d: plan was created on device %d, the current device is %d", k,
+                        p->device, dev);
         if (jb.in == nullptr || jb.out == nullptr)
             return fail(CBESSFM_ERR_INVALID_ARG, "job %d: in/out is NULL", k);
         if (jb.n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "job %d: n_samples < 1", k);
@@ -84,10 +92,8 @@ static cbessfm_status batch_create_body(const cbessfm_job* jobs, int njobs, cbes
         by_shape[std::make_tuple(p->n_fft, p->n_sb, (int)p->storage, p->per_pol)].push_back(k);
     }
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
     int n_sm = 0;
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_fail(e, "device query");
 
     // the groups and work items are built in host containers before the batch and its device

@@ -184,10 +184,18 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
     int prefix[kNoallocMaxJobs + 1];
     int np = 0, n_sb = 0, region = 0;
     bool any_taps = false;
+    // the static array and the plans' tables must be on the same (current) device
+    int dev = 0;
+    cudaError_t e = cudaSuccess;
     for (int k = 0; k < njobs; ++k) {
         const cbessfm_job& jb = jobs[k];
         const PlanImpl* p = plan_impl(jb.plan);
         if (p == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "job %d: plan is NULL", k);
+        if (k == 0 && (e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        if (p->device != dev)
+            return fail(CBESSFM_ERR_INVALID_ARG,
+                        "job %d: plan was created on device %d, the current device is %d", k,
+                        p->device, dev);
         if (jb.in == nullptr || jb.out == nullptr)
             return fail(CBESSFM_ERR_INVALID_ARG, "job %d: in/out is NULL", k);
         if (jb.n_samples < 1) return fail(CBESSFM_ERR_INVALID_ARG, "job %d: n_samples < 1", k);
@@ -255,9 +263,6 @@ extern "C" cbessfm_status cbessfm_batch_run_noalloc(const cbessfm_job* jobs, int
         prefix[k + 1] = (int)n;
     }
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(CBESSFM_ERR_UNSUPPORTED, "device index %d", dev);
     unsigned char* scratch = nullptr;
     int n_sm = 0;

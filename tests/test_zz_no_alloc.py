@@ -27,13 +27,26 @@ def _entry():
     return cbessfm, lib, fn
 
 
-def test_noalloc_batch_matches_plain_entry_point_on_two_calls():
+CASE_SETS = {
+    # N' = 256, 3 bands, mixed lengths, steps and tap counts
+    "np256": [Case(3, 256, 16, 2, 5, 0.3, 5000, sample_rate=192e9, seed=1),
+              Case(3, 256, 16, 2, 5, 0.3, 777, sample_rate=192e9, seed=2),
+              Case(3, 256, 16, 8, 7, 0.12, 20000, sample_rate=192e9, seed=3),
+              Case(3, 256, 16, 1, 5, 0.5, 96, sample_rate=192e9, seed=4)],
+    # N' = 1024, 5 bands (the two-pass layout, staged 11-tap filters next to unstaged 7-tap
+    # ones), step counts in ascending order, so the call's longest-first reordering of the jobs
+    # must still write each output to its own job
+    "np1024": [Case(5, 1024, 256, 1, 11, 0.3, 9000, sample_rate=640e9, seed=5),
+               Case(5, 1024, 256, 3, 7, 0.3, 4000, sample_rate=640e9, seed=6),
+               Case(5, 1024, 256, 8, 11, 0.12, 12000, sample_rate=640e9, seed=7)],
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASE_SETS))
+def test_noalloc_batch_matches_plain_entry_point_on_two_calls(name):
     import torch
     cbessfm, lib, fn = _entry()
-    cases = [Case(3, 256, 16, 2, 5, 0.3, 5000, sample_rate=192e9, seed=1),
-             Case(3, 256, 16, 2, 5, 0.3, 777, sample_rate=192e9, seed=2),
-             Case(3, 256, 16, 8, 7, 0.12, 20000, sample_rate=192e9, seed=3),
-             Case(3, 256, 16, 1, 5, 0.5, 96, sample_rate=192e9, seed=4)]
+    cases = CASE_SETS[name]
     plans = [make_plan(c, case_taps(c)) for c in cases]
     xs = [to_storage(random_field(c)[0], 0) for c in cases]
     ys = [torch.empty_like(x) for x in xs]
