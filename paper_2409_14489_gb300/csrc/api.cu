@@ -149,10 +149,10 @@ bool choose_layout(PlanImpl& p, int tb, int tpf) {
     const int tw = chain_tw_bytes(fft_tw_size(n_fft, E));
     const int tw_taps = tw + (p.nchunks == 3 ? chain_taps_bytes(bands) : 0);
     if (chain_packed(n_fft, per_pol)) {
-        // one exchange array per group; its intensity row, (cos, sin) row (one spare per 32) and
+        // one exchange array per group; its intensity row, (cos, sin) row (one spare per 16) and
         // the parked slots fit inside it
         // the array grows past its exchange size when long filters need longer intensity rows
-        const int rows_bytes = 4 * p.pstride + 8 * (n_fft + n_fft / 32) + 8 * kParkSlots * 2 * tpf;
+        const int rows_bytes = 4 * p.pstride + 8 * (n_fft + n_fft / 16) + 8 * kParkSlots * 2 * tpf;
         const int xl_bytes = round_up(std::max(16 * xpad_len_s(n_fft, fft_xsh(n_fft, E)), rows_bytes), 128);
         const int region = round_up(bands * xl_bytes, 128);
         int tbl = tw_taps;

@@ -315,7 +315,9 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     constexpr int SH = fft_xsh(NP, E);                 // exchange padding: one per 2^SH
     constexpr int TPF = NP / E;                        // threads per (subband, polarization)
     constexpr int XL = 2 * xpad_len_s(NP, SH);         // float2 per group exchange array
-    constexpr int CSH = PACKED ? 5 : 4;                // (cos, sin) rows: one spare per 2^CSH
+    // (cos, sin) rows: one spare per 16, so the FIR lanes' stores (16 samples apart, x and y
+    // lanes 16 apart in the packed layout) and the slot reads are both conflict-free
+    constexpr int CSH = 4;
     constexpr int CSL = NP + (NP >> CSH);              // float2 per (cos, sin) row
     // DEMUX/MUX twiddles by one table value per polyphase row times a per-slot factor; 32 slots
     // keep the plain table read: they leave no registers for the product
