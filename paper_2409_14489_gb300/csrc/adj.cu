@@ -44,20 +44,6 @@ __device__ __forceinline__ void fir8_acc(const ChainArgs& a, const float4* __res
     }
 }
 
-// Read-only load that the compiler may not merge with another load of the same address (keeping
-// a table value live across a whole step costs registers that the step needs).
-__device__ __forceinline__ float ldg_once(const float* p) {
-    float v;
-    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ float2 ldg2_once(const float2* p) {
-    float2 v;
-    asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
-    return v;
-}
-
 // write value v of row sample n (and its circular halo copies) into swizzled row `row`
 template <int NP, int E>
 __device__ __forceinline__ void row_store(float* row, int mb, int n, int H, float v) {
@@ -252,15 +238,27 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
                 if (ph == 0) {
                     float rs = 0.f;
 #pragma unroll
-                    for (int t = 0; t < E; ++t) {
-                        const int o = 2 * (j + TPF * t);
-                        const float2 dz = c_conj(x[t]);
-                        const float2 hv = ldg2_once(h + j + TPF * t);
-                        const float2 zs = c_sub(c_scale(c_mulc(z1[o], hv), NPf), c_scale(dz, inv_NP));
-                        if (real) sz[o] = zs;
-                        const float2 gw = sg[o];
-                        rs = fmaf(-kappa(t), gw.x * dz.y - gw.y * dz.x, rs);
-                        x[t] = gw;
+                    for (int t0 = 0; t0 < E; t0 += 4) {
+                        // four slots' scratch and table loads issued together before their
+                        // stores (the pass is bound by L2 round trips: 0.46 ms of c4's 2.31)
+                        float2 zv[4], hw[4], gv[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int o = 2 * (j + TPF * (t0 + q));
+                            zv[q] = z1[o];
+                            hw[q] = __ldg(h + j + TPF * (t0 + q));
+                            gv[q] = sg[o];
+                        }
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const int t = t0 + q;
+                            const int o = 2 * (j + TPF * t);
+                            const float2 dz = c_conj(x[t]);
+                            const float2 zs = c_sub(c_scale(c_mulc(zv[q], hw[q]), NPf), c_scale(dz, inv_NP));
+                            if (real) sz[o] = zs;
+                            rs = fmaf(-kappa(t), gv[q].x * dz.y - gv[q].y * dz.x, rs);
+                            x[t] = gv[q];
+                        }
                     }
                     rho_part += (double)rs;
                 }
