@@ -162,7 +162,11 @@ cbessfm_status cbessfm_backpropagate_checkpointed(const cbessfm_plan* plan, cons
  * adjoint of the rotation, the coupled-band FIR (transposed taps) and the intensity.  dL/drho
  * (the ratio enters only the first and the last GVD, Sec. III-C) is accumulated as one term per
  * step built from exp(j theta) - 1, which keeps its FP32 error at the level of the other
- * gradients on long links where the two end terms nearly cancel.
+ * gradients on long links where the two end terms nearly cancel.  With the per-polarization NLPR
+ * (cbessfm_set_nlpr_mode, Eqs. (NLPR_polx/poly)) the phase gradients of the two polarizations
+ * enter as their sum S and difference D: the FIR adjoint runs over S with all taps and over D
+ * with the coupling taps (i != l) at 1/3, and the tap gradient adds sum_k D_i[k] (Px_l -
+ * Py_l)[k - m] / 3 for i != l; the plan's mode must be the one of the checkpointed forward.
  */
 cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, double* grad_coeffs,
                             double* grad_ratio, void* grad_in, void* workspace, size_t ws_bytes,
@@ -310,9 +314,11 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
  * (w_il = (3/2) c_il for l != i), so with equal intensities in x and y both forms agree; the
  * FIR index is [k - m] in both.  The per-polarization form needs shared memory for a second set
  * of intensity rows: CBESSFM_ERR_UNSUPPORTED (plan unchanged) if they do not fit, and for
- * FP16/BF16 storage.  Gradients (cbessfm_grad) and cbessfm_batch_run_noalloc support mode 0
- * only; cbessfm_batch_* runs both.  Synchronous with respect to the host, not to the
- * device: do not call while launches of the plan are in flight.
+ * FP16/BF16 storage.  cbessfm_batch_* and the gradients run both modes (the per-polarization
+ * adjoint needs further rows of shared memory: CBESSFM_ERR_UNSUPPORTED from
+ * cbessfm_backpropagate_checkpointed / cbessfm_grad where they do not fit, e.g. 5 subbands of
+ * N' = 1024); cbessfm_batch_run_noalloc supports mode 0 only.  Synchronous with respect to the
+ * host, not to the device: do not call while launches of the plan are in flight.
  */
 cbessfm_status cbessfm_set_nlpr_mode(cbessfm_plan* plan, int per_polarization);
 

@@ -1,4 +1,7 @@
-// adj.cu -- reverse-mode gradient (adjoint) of the CB-ESSFM chain (differentiation form).
+// adj.cu -- reverse-mode gradient (adjoint) of the CB-ESSFM chain (differentiation form): the
+// C-ABI entry points, the workspace layout, the launches and the FP64 reductions.  The adjoint
+// kernel itself is in adj_kernel.cuh (Manakov form launched here, per-polarization form from
+// adj_perpol.cu).
 //
 // The paper trains its taps offline with finite-difference gradients (Sec. III-B) and names
 // automatic differentiation as the way to per-step taps; this file is the hand-written adjoint
@@ -28,463 +31,10 @@
 #include <vector>
 
 #include "block_count.h"
-#include "fwd_kernel.cuh"
+#include "adj_kernel.cuh"
 #include "internal.h"
 
 namespace cbessfm {
-
-// The forward kernel's windowed FIR (fir8) with the 9-to-12-tap fast path.
-template <int E>
-__device__ __forceinline__ void fir8_acc(const ChainArgs& a, const float4* __restrict__ wbase,
-                                         const float* __restrict__ rows0, int k0, float (&acc)[8]) {
-    if (a.nchunks == 3) {
-        fir8<E, 3>(a, wbase, rows0, a.pstride, k0, acc);
-    } else {
-        fir8<E, 0>(a, wbase, rows0, a.pstride, k0, acc);
-    }
-}
-
-// write value v of row sample n (and its circular halo copies) into swizzled row `row`
-template <int NP, int E>
-__device__ __forceinline__ void row_store(float* row, int mb, int n, int H, float v) {
-    row[pswz<E>(mb + n)] = v;
-    if (n < H) row[pswz<E>(mb + n + NP)] = v;
-    if (n >= NP - H) row[pswz<E>(mb + n - NP)] = v;
-}
-
-template <int NP>
-__global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) {
-    constexpr int E = fft_slots(NP);
-    constexpr int TPF = NP / E;
-    constexpr int XL = 2 * xpad_len(NP);
-    constexpr int CSL = NP + NP / 16;
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ float2 s_rot[kRotTable];
-    const ThreadPos tp = thread_pos<NP>(a.n_sb);
-    for (int k = tp.tid; k < kRotTable; k += blockDim.x) s_rot[k] = __ldg(a.rot_tbl + k);
-    // FFT twiddles staged after the G block regions
-    float2* const s_tw = reinterpret_cast<float2*>(smem + (size_t)a.G * a.region_bytes);
-    for (int k = tp.tid; k < fft_tw_size(NP); k += blockDim.x) s_tw[k] = __ldg(a.fft_tw + k);
-    const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
-    const int N = a.N, n_sb = a.n_sb;
-
-    // ---- shared-memory layout of this block's region ----------------------------------------
-    unsigned char* region = smem + (size_t)g * a.region_bytes;
-    float2* e = reinterpret_cast<float2*>(region) + gi * XL + p;          // exchange [0, 17 N)
-    float* prow0 = reinterpret_cast<float*>(region + a.nlpr_off);         // intensity rows
-    float2* csbase = reinterpret_cast<float2*>(prow0 + n_sb * a.pstride); // (cos, sin) rows
-    float* trow0 = reinterpret_cast<float*>(csbase + n_sb * CSL);         // G_theta rows
-    float* gprow0 = trow0 + n_sb * a.pstride;                              // G_P rows [l][n]
-    float* gtplain = gprow0 + n_sb * NP;                                   // G_theta rows [i][n]
-    float* accw = gtplain + n_sb * NP;                                     // tap-gradient sums
-    const int n_acc = n_sb * n_sb * a.ntaps_pad;
-    double* acc_rho = reinterpret_cast<double*>(accw + n_acc);          // 16-byte aligned slot
-    const int mb = a.H + a.p_off;
-
-    const long long total = (long long)a.batch * a.n_blocks;
-    const long long item = (long long)blockIdx.x * a.G + g;
-    const bool real = item < total;
-    const int seq = real ? (int)(item / a.n_blocks) : 0;
-    const int blk = real ? (int)(item % a.n_blocks) : 0;
-    const long long gblk = real ? item : 0;
-    const GroupBar<NP, E> bar{1 + g * n_sb + gi};
-    const float2* ck = a.ckpt + (size_t)gblk * (size_t)(a.n_st + 2) * 2 * N + (size_t)gi * NP * 2 + p;
-    auto load_ckpt = [&](int c, float2 (&v)[E]) {
-        const float2* src = ck + (size_t)c * 2 * N;
-#pragma unroll
-        for (int t = 0; t < E; ++t) v[t] = src[2 * (j + TPF * t)];
-    };
-    for (int k = rem; k < n_acc + 4; k += TB) accw[k] = 0.f;
-
-    // ---- 1. stage dL/d(out) of the kept samples (zero elsewhere), DFT_N + DEMUX ----------
-    float2* stage = reinterpret_cast<float2*>(region);                    // [N] (x, y) pairs
-    const int lo = a.n_ov / 2;
-    const long long base = (long long)blk * a.V - lo;
-    for (int n = rem; n < 2 * N; n += TB) {
-        const int smp = n >> 1;
-        const long long gidx = base + smp;
-        const bool keep = real && smp >= lo && smp < lo + a.V && gidx < a.L;
-        stage[n] = keep ? a.gout[2 * ((long long)seq * a.L + gidx) + (n & 1)] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    float2 x[E];
-#pragma unroll
-    for (int t = 0; t < E; ++t) x[t] = stage[2 * (n_sb * (j + TPF * t) + gi) + p];
-    __syncthreads();
-    fft_regs<NP, E, false, true>(x, j, e, s_tw, bar);
-    bar();
-#pragma unroll
-    for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = x[t];
-    __syncthreads();
-    const int ci = -N / 2 + gi * NP + NP / 2;
-    {
-        // DEMUX as in the forward chain: W_N^(K r) = W_N^(K_0 r) times the slot factor of (r, t)
-        const float2* eb = reinterpret_cast<const float2*>(region) + p;
-        const float2* td = a.mix_td;
-        int K0 = ci + j;
-        K0 += (K0 < 0) ? N : 0;
-#pragma unroll
-        for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
-        for (int r = 0; r < n_sb; ++r) {
-            const float2* er = eb + r * XL;
-            const float2 w0 = __ldg(a.mix_tw + (size_t)r * N + K0);
-#pragma unroll
-            for (int t = 0; t < E; ++t) {
-                const int kap = j + TPF * t;
-                int K = ci + (kap < NP / 2 ? kap : kap - NP);
-                K += (K < 0) ? N : 0;
-                const float2 w = c_mul(w0, __ldg(td + r * E + t));
-                x[t] = c_add(x[t], c_mul(er[2 * xpad(K & (NP - 1))], w));
-            }
-        }
-    }
-    __syncthreads();
-    // x now holds G for the spectrum after the last GVD.
-    // kdisp of slot t: 2 pi^2 beta2 L_step (R/N)^2 (2 c_i k' + k'^2), k' the centred lowpass bin
-    // (the table value of the plan, with the integer part exact in FP32)
-    auto kappa = [&](int t) {
-        const int kap = j + TPF * t;
-        const int kp = kap < NP / 2 ? kap : kap - NP;
-        const int cc = -a.N / 2 + gi * NP + NP / 2;
-        return a.kd0 * (float)(2 * cc * kp + kp * kp);
-    };
-    // Splitting-ratio gradient.  With Q(Z) = sum_bins kdisp Im(conj(G_Z) Z), the ratio enters
-    // the first and the last GVD only, so dL/drho = Q(Z_0) - Q(Z_N) (Z_s: spectrum entering step
-    // s, Z_N the final one).  Q is unchanged by a GVD, so the difference telescopes into one
-    // term per step: Q(Z_s) - Q(W_s), W_s the spectrum leaving the rotation.  With
-    // psi = exp(j theta) - 1, D_Z = DFT(psi u) and D_G = DFT(conj(psi) G_v + 2 G_P u),
-    //   Q(Z_s) - Q(W_s) = sum kdisp Im(conj(D_G) Z_s - conj(G_W) D_Z),
-    // where D_Z and D_G come from their own small sources.  On long links the two end terms
-    // are thousands of times the result, and their FP32 rounding would dominate it.  Z_s is
-    // rebuilt backwards, Z_s = NP conj(h_s) Z_(s+1) - D_Z / NP (|h_s| = 1/NP), from the final
-    // spectrum, and the adjoint's own G for Z_s becomes NP G_W + D_G.  kdisp omits the
-    // subband-centre part (an exact invariant), which also keeps the two terms of a step from
-    // cancelling when theta is large.  Each thread sums its 16 bins of a term in FP32 (those
-    // rounding errors are independent across threads and steps) and adds the partial to an
-    // FP64 total once per term; GB300's FP64 rate makes per-bin FP64 arithmetic costly.
-    double rho_part = 0.0;
-    const float NPf = (float)NP;
-    const float inv_NP = 1.0f / NPf;
-    float2* const sg = a.stash + (size_t)gblk * 4 * N + (size_t)gi * NP * 2 + p;   // G_W
-    float2* const sz = sg + 2 * N;                                               // Z_s
-
-    // ---- 2. steps, last to first ----------------------------------------------------------
-    float2* cs_mine = csbase + gi * CSL;                                    // psi rows
-    const int k0 = E * j + (E / 2) * p;                                    // FIR outputs k0 ..
-#pragma unroll 1
-    for (int s = a.n_st - 1; s >= 0; --s) {
-        const float2* h = a.gvd + (size_t)((s < a.n_st - 1 ? 1 : 2) * n_sb + gi) * NP;
-        // G_W = conj(h) G_(Z_(s+1)), kept in the block's scratch when dL/drho is wanted
-        const bool rho = a.want_ratio != 0;
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-            x[t] = c_mulc(x[t], __ldg(h + j + TPF * t));
-            if (real && rho) sg[2 * (j + TPF * t)] = x[t];
-        }
-        {
-            float2 u[E];
-            load_ckpt(1 + s, u);
-            // while the FIR runs, this thread's slots of the exchange array keep what the
-            // transform after it needs: the step's time samples (the source of D_Z) on the ratio
-            // path, G_W otherwise (the ratio path has G_W in its scratch field).  The array is
-            // idle until that transform, and no other thread still reads these slots: the last
-            // pass of every transform loads exactly the thread's own slot elements, and before
-            // the first step only barrier-separated DEMUX reads touched the array.
-#pragma unroll
-            for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = rho ? u[t] : x[t];
-            float* prow = prow0 + gi * a.pstride;
-            // both lanes of an x/y pair hold every slot's intensity after the shuffle: lane p
-            // stores the slots t with t % 2 == p (no branch on the polarization)
-#pragma unroll
-            for (int t2 = 0; t2 < E; t2 += 2) {
-                float pw0 = fmaf(u[t2].x, u[t2].x, u[t2].y * u[t2].y);
-                float pw1 = fmaf(u[t2 + 1].x, u[t2 + 1].x, u[t2 + 1].y * u[t2 + 1].y);
-                pw0 += __shfl_xor_sync(0xffffffffu, pw0, 1);
-                pw1 += __shfl_xor_sync(0xffffffffu, pw1, 1);
-                row_store<NP, E>(prow, mb, j + TPF * (t2 + p), a.H, p ? pw1 : pw0);
-            }
-        }
-        __syncthreads();
-        {
-            const float4* wb = reinterpret_cast<const float4*>(
-                a.taps + (size_t)(s * n_sb + gi) * n_sb * a.ntaps_pad);
-#pragma unroll
-            for (int h8 = 0; h8 < E / 16; ++h8) {
-                float acc[8];
-                fir8_acc<E>(a, wb, prow0, k0 + 8 * h8, acc);
-                float2* dst = cs_mine + cpad(k0 + 8 * h8);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) dst[q] = rotation_psi(acc[q], s_rot);
-            }
-        }
-        __syncthreads();
-        // Two inverse transforms share one call site: D_Z = conj(IDFT(conj(psi u))), then G_v.
-        // Between them: Z_s = NP conj(h) Z_(s+1) - D_Z / NP, the G_W part of the ratio term, and
-        // G_W back into x as the second transform's input.
-        {
-            const float2* z1 = s == a.n_st - 1 ? ck + (size_t)(a.n_st + 1) * 2 * N : sz;
-            if (!rho) {
-#pragma unroll
-                for (int t = 0; t < E; ++t) x[t] = e[2 * xpad(j + TPF * t)];      // G_W
-            }
-#pragma unroll 1
-            for (int ph = rho ? 0 : 1; ph < 2; ++ph) {
-                if (ph == 0) {
-#pragma unroll
-                    for (int t = 0; t < E; ++t)                                    // u from e
-                        x[t] = c_conj(c_mul(cs_mine[cpad(j + TPF * t)], e[2 * xpad(j + TPF * t)]));
-                }
-                fft_regs<NP, E, true, true>(x, j, e, s_tw, bar);
-                if (ph == 0) {
-                    float rs = 0.f;
-#pragma unroll
-                    for (int t0 = 0; t0 < E; t0 += 4) {
-                        // four slots' scratch and table loads issued together before their
-                        // stores (the pass is bound by L2 round trips: 0.46 ms of c4's 2.31)
-                        float2 zv[4], hw[4], gv[4];
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int o = 2 * (j + TPF * (t0 + q));
-                            zv[q] = z1[o];
-                            hw[q] = __ldg(h + j + TPF * (t0 + q));
-                            gv[q] = sg[o];
-                        }
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int t = t0 + q;
-                            const int o = 2 * (j + TPF * t);
-                            const float2 dz = c_conj(x[t]);
-                            const float2 zs = c_sub(c_scale(c_mulc(zv[q], hw[q]), NPf), c_scale(dz, inv_NP));
-                            if (real) sz[o] = zs;
-                            rs = fmaf(-kappa(t), gv[q].x * dz.y - gv[q].y * dz.x, rs);
-                            x[t] = gv[q];
-                        }
-                    }
-                    rho_part += (double)rs;
-                }
-            }
-        }
-        {
-            // G_theta and the first part of D_G's source, conj(psi) G_v
-            float2 u[E];
-            load_ckpt(1 + s, u);
-            float* trow = trow0 + gi * a.pstride;
-#pragma unroll
-            for (int t = 0; t < E; ++t) {
-                const float2 ps = cs_mine[cpad(j + TPF * t)];
-                const float2 v = c_mul(u[t], make_float2(1.0f + ps.x, ps.y));
-                float gt = -(x[t].x * v.y - x[t].y * v.x);                 // -Im(conj(G_v) v)
-                gt += __shfl_xor_sync(0xffffffffu, gt, 1);
-                // both lanes hold the sum: lane p stores the odd or even slots (no branch on p)
-                if ((t & 1) == p) {
-                    const int n = j + TPF * t;
-                    row_store<NP, E>(trow, mb, n, a.H, gt);
-                    gtplain[gi * NP + n] = gt;
-                }
-                // conj(psi) G_v (the ratio path adds G_v back in the spectral domain as NP G_W)
-                x[t] = rho ? c_mulc(x[t], ps) : c_mulc(x[t], make_float2(1.0f + ps.x, ps.y));
-            }
-        }
-        __syncthreads();
-        // x (conj(psi) G_v) waits in this thread's own slots of the exchange array, idle until the
-        // step's last transform, so the correlation below has the registers to itself
-#pragma unroll
-        for (int t = 0; t < E; ++t) e[2 * xpad(j + TPF * t)] = x[t];
-        {
-            // dL/dw[s][i][l][m] = sum_k G_theta_i[k] P_l[k - m].  Each (i, l) pair is handled by
-            // 16 consecutive lanes; lane `sub` takes the KW-sample chunks k0 = 16 KW r + KW sub
-            // (its float4 loads are 16 bytes apart across lanes: no bank conflicts), loads one
-            // intensity window for all 12 taps of the 9-to-12-tap case (KW + 12 - 1 samples), and
-            // accumulates the 12 tap sums in registers; a 16-lane shuffle reduction then gives
-            // each pair's sums to one lane, which stores them.  Other tap counts use the generic
-            // loop below.
-            const int nseg = NP / 16;
-            const int n_pairs = n_sb * n_sb;
-            const int lanes = (TB % 16 == 0 && a.nchunks == 3 && NP >= 64) ? TB : 0;
-            for (int base_t = 0; lanes > 0 && base_t < n_pairs * 16; base_t += lanes) {
-                const int t16 = base_t + rem;
-                const bool act = t16 < n_pairs * 16;
-                const int pair = act ? t16 >> 4 : 0, sub = t16 & 15;
-                const int i = pair / n_sb, l = pair - i * n_sb;
-                const float* gtr = gtplain + i * NP;
-                const float* pr = prow0 + l * a.pstride;
-                float acc[12];
-#pragma unroll
-                for (int m = 0; m < 12; ++m) acc[m] = 0.f;
-                if (act) {
-                    constexpr int KW = NP >= 128 ? 8 : 4;           // samples per lane and pass
-#pragma unroll 2
-                    for (int it = 0; it < NP / (16 * KW); ++it) {
-                        const int k0 = KW * sub + 16 * KW * it;
-                        float g[KW];
-#pragma unroll
-                        for (int c4 = 0; c4 < KW / 4; ++c4) {
-                            const float4 g4 = *reinterpret_cast<const float4*>(gtr + k0 + 4 * c4);
-                            g[4 * c4] = g4.x; g[4 * c4 + 1] = g4.y; g[4 * c4 + 2] = g4.z;
-                            g[4 * c4 + 3] = g4.w;
-                        }
-                        // P_l[k0 + q - m], m = -nc + mi (mi in [0, 12)): window start
-                        // k0 + nc - 11, aligned because (H + p_off + nc + 1) % 4 == 0
-                        const int ws = mb + k0 + a.nc - 11;
-                        float win[KW + 12];
-#pragma unroll
-                        for (int e4 = 0; e4 < KW / 4 + 3; ++e4) {
-                            const float4 v = *reinterpret_cast<const float4*>(pr + pswz<E>(ws + 4 * e4));
-                            win[4 * e4] = v.x; win[4 * e4 + 1] = v.y; win[4 * e4 + 2] = v.z;
-                            win[4 * e4 + 3] = v.w;
-                        }
-#pragma unroll
-                        for (int mi = 0; mi < 12; ++mi)
-#pragma unroll
-                            for (int q = 0; q < KW; ++q) acc[mi] = fmaf(g[q], win[q - mi + 11], acc[mi]);
-                    }
-                }
-#pragma unroll
-                for (int mi = 0; mi < 12; ++mi) {
-#pragma unroll
-                    for (int o = 8; o > 0; o >>= 1) acc[mi] += __shfl_xor_sync(0xffffffffu, acc[mi], o);
-                }
-                if (act && sub == 0) {
-                    float* dst = accw + (i * n_sb + l) * a.ntaps_pad;
-#pragma unroll
-                    for (int mi = 0; mi < 12; ++mi) dst[mi] = acc[mi];
-                }
-            }
-            if (lanes == 0) {
-                // blocks narrower than 16 lanes (small N'): one atomic per segment and tap chunk
-                for (int w = rem; w < n_pairs * nseg; w += TB) {
-                    const int pair = w / nseg, seg = w - pair * nseg;
-                    const int i = pair / n_sb, l = pair - i * n_sb;
-                    const int ks = 16 * seg;
-                    const float* tr = trow0 + i * a.pstride;
-                    const float* pr = prow0 + l * a.pstride;
-                    for (int c = 0; c < a.nchunks; ++c) {
-                        const int m = mb + ks + a.nc - 4 * c - 3;
-                        float win[20];
-#pragma unroll
-                        for (int e4 = 0; e4 < 5; ++e4) {
-                            const float4 v = *reinterpret_cast<const float4*>(pr + pswz<E>(m + 4 * e4));
-                            win[4 * e4] = v.x; win[4 * e4 + 1] = v.y; win[4 * e4 + 2] = v.z;
-                            win[4 * e4 + 3] = v.w;
-                        }
-                        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) {
-                            const float gq = tr[pswz<E>(mb + ks + q)];
-                            s0 = fmaf(gq, win[q + 3], s0);
-                            s1 = fmaf(gq, win[q + 2], s1);
-                            s2 = fmaf(gq, win[q + 1], s2);
-                            s3 = fmaf(gq, win[q], s3);
-                        }
-                        float* acc = accw + (i * n_sb + l) * a.ntaps_pad + 4 * c;
-                        atomicAdd(acc, s0);
-                        atomicAdd(acc + 1, s1);
-                        atomicAdd(acc + 2, s2);
-                        atomicAdd(acc + 3, s3);
-                    }
-                }
-            }
-            // G_P_l[n] = sum_i sum_m' wt[s][l][i][m'] G_theta_i[n - m'] (transposed taps)
-            const float4* wb = reinterpret_cast<const float4*>(
-                a.taps_t + (size_t)(s * n_sb + gi) * n_sb * a.ntaps_pad);
-#pragma unroll
-            for (int h8 = 0; h8 < E / 16; ++h8) {
-                float acc[8];
-                fir8_acc<E>(a, wb, trow0, k0 + 8 * h8, acc);
-                float4* dst = reinterpret_cast<float4*>(gprow0 + gi * NP + k0 + 8 * h8);
-                dst[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
-                dst[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
-            }
-        }
-        __syncthreads();
-        {
-            // publish and clear this step's tap-gradient sums
-            if (real) {
-                float* gp = a.gpart + (size_t)gblk * ((size_t)a.n_st * n_acc + 4) + (size_t)s * n_acc;
-                for (int k = rem; k < n_acc; k += TB) gp[k] = accw[k];
-            }
-            float2 u[E];
-            load_ckpt(1 + s, u);
-            const float* gpr = gprow0 + gi * NP;
-#pragma unroll
-            for (int t = 0; t < E; ++t) {
-                const float gp2 = 2.f * gpr[j + TPF * t];
-                const float2 xv = e[2 * xpad(j + TPF * t)];               // parked above
-                x[t] = make_float2(fmaf(gp2, u[t].x, xv.x), fmaf(gp2, u[t].y, xv.y));
-            }
-        }
-        __syncthreads();
-        for (int k = rem; k < n_acc; k += TB) accw[k] = 0.f;
-        // D_G = DFT(conj(psi) G_v + 2 G_P u); G for Z_s = NP G_W + D_G; the D_G part of the ratio
-        fft_regs<NP, E, false, true>(x, j, e, s_tw, bar);
-        if (rho) {
-            float rs = 0.f;
-#pragma unroll
-            for (int t = 0; t < E; ++t) {
-                const int o = 2 * (j + TPF * t);
-                const float2 zs = sz[o];
-                rs = fmaf(kappa(t), x[t].x * zs.y - x[t].y * zs.x, rs);
-                const float2 gw = sg[o];
-                x[t] = make_float2(fmaf(NPf, gw.x, x[t].x), fmaf(NPf, gw.y, x[t].y));
-            }
-            rho_part += (double)rs;
-        }
-    }
-
-    // ---- 3. first GVD, adjoint of entry (MUX + IDFT_N), scatter to G_in ---------------------
-    atomicAdd(acc_rho, rho_part);                 // warps may span several small blocks
-    {
-        const float2* h = a.gvd + (size_t)gi * NP;
-#pragma unroll
-        for (int t = 0; t < E; ++t) x[t] = c_mulc(x[t], __ldg(h + j + TPF * t));
-    }
-    __syncthreads();
-    if (real && rem == 0) {
-        float* gp = a.gpart + (size_t)gblk * ((size_t)a.n_st * n_acc + 4) + (size_t)a.n_st * n_acc;
-        *reinterpret_cast<double*>(gp) = *acc_rho;                       // 16-byte aligned
-    }
-    if (a.gin == nullptr) return;                                         // uniform
-    {
-        float2* ex = reinterpret_cast<float2*>(region) + p;
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int kap = j + TPF * t;
-            int K = ci + (kap < NP / 2 ? kap : kap - NP);
-            if (K < 0) K += N;
-            ex[2 * xpad(K)] = x[t];
-        }
-        __syncthreads();
-        // MUX as in the forward chain: W_N^(K gi) = W_N^((j + NP q) gi) W_N^((N'/E) t gi)
-        const float2* wr = a.mix_tw + (size_t)gi * N;
-        const float2* tm = a.mix_tm + gi * E;
-#pragma unroll
-        for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
-        for (int q = 0; q < n_sb; ++q) {
-            const float2 w0 = __ldg(wr + j + NP * q);
-#pragma unroll
-            for (int t = 0; t < E; ++t) {
-                const int K = j + TPF * t + NP * q;
-                const float2 w = c_mul(w0, __ldg(tm + t));
-                x[t] = c_add(x[t], c_mulc(ex[2 * xpad(K)], w));
-            }
-        }
-    }
-    __syncthreads();
-    fft_regs<NP, E, true, true>(x, j, e, s_tw, bar);
-    if (real) {
-        long long pos = base % a.L;
-        if (pos < 0) pos += a.L;
-        float* gin = reinterpret_cast<float*>(a.gin) + 4 * (long long)seq * a.L + 2 * p;
-#pragma unroll
-        for (int t = 0; t < E; ++t) {
-            const int n = n_sb * (j + TPF * t) + gi;
-            long long q = pos + n;
-            q -= (q / a.L) * a.L;
-            atomicAdd(gin + 4 * q, x[t].x);
-            atomicAdd(gin + 4 * q + 1, x[t].y);
-        }
-    }
-}
 
 // FP64 sum of the per-block partial gradients: out[k] = sum_b part[b][k].
 __global__ void reduce_blocks_kernel(const float* __restrict__ part, long long n_blocks, int stride,
@@ -544,6 +94,7 @@ cudaError_t launch_np_adj(const ChainArgs& a, int threads, cudaStream_t st) {
     const long long grid = (total + a.G - 1) / a.G;
     if (grid <= 0) return cudaSuccess;
     const size_t smem = (size_t)a.G * a.region_bytes;
+    if (a.per_pol) return launch_adj_per_pol(NP, ADJ, a, threads, st);   // adj_perpol.cu
     if constexpr (ADJ) {
         const size_t smem_a = smem + chain_tw_bytes(fft_tw_size(NP));   // + staged twiddles
         cudaError_t e = cudaFuncSetAttribute(cbessfm_adj_kernel<NP>,
@@ -579,11 +130,14 @@ int round_up_i(long long v, int m) { return (int)((v + m - 1) / m * m); }
 
 // Shared-memory region of one block for the adjoint: exchange, intensity, (cos, sin), G_theta
 // (swizzled with halo, and plain), G_P rows and the accumulators.
+// The per-polarization form adds, from the next 128-byte boundary, the Px - Py rows and the
+// D = G_tx - G_ty rows (swizzled, with halo) and the G_Dp rows.
 int adj_region_bytes(const PlanImpl& p) {
     const int NP = p.n_fft, nsb = p.n_sb;
-    const long long bytes = round_up_i(16LL * xpad_len(p.N), 128) + 4LL * nsb * p.pstride +
-                            8LL * nsb * xpad_len(NP) + 4LL * nsb * p.pstride + 8LL * nsb * NP +
-                            4LL * (nsb * nsb * p.ntaps_pad + 4);
+    long long bytes = round_up_i(16LL * xpad_len(p.N), 128) + 4LL * nsb * p.pstride +
+                      8LL * nsb * xpad_len(NP) + 4LL * nsb * p.pstride + 8LL * nsb * NP +
+                      4LL * (nsb * nsb * p.ntaps_pad + 4);
+    if (p.per_pol) bytes = round_up_i(bytes, 128) + 8LL * nsb * p.pstride + 4LL * nsb * NP;
     return round_up_i(bytes, 128);
 }
 
@@ -619,8 +173,6 @@ cbessfm_status check_common(const cbessfm_plan* plan, int64_t n_samples, int bat
     if (p == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     if (p->storage != CBESSFM_C64)
         return fail(CBESSFM_ERR_UNSUPPORTED, "gradients need complex64 storage");
-    if (p->per_pol)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "gradients cover the Manakov NLPR only");
     if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
     if (too_many_blocks(blocks_for(n_samples, p->V), batch))
         return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks");
@@ -631,8 +183,8 @@ cbessfm_status check_common(const cbessfm_plan* plan, int64_t n_samples, int bat
     if (ws_bytes < l.total)
         return fail(CBESSFM_ERR_INVALID_ARG, "workspace of %zu bytes is smaller than %zu", ws_bytes, l.total);
     if (adj_region_bytes(*p) + chain_tw_bytes(fft_tw_size(p->n_fft)) > kMaxDynSmem)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "the adjoint of a %d-sample block does not fit shared memory",
-                    p->N);
+        return fail(CBESSFM_ERR_UNSUPPORTED, "the adjoint of a %d-sample block%s does not fit shared memory",
+                    p->N, p->per_pol ? " with the per-polarization NLPR" : "");
     *pp = p;
     return CBESSFM_OK;
 }

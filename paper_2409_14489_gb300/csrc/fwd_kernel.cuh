@@ -730,11 +730,12 @@ __global__ void __launch_bounds__(chain_max_threads(NP, PERPOL), chain_min_ctas(
                                        s_taps, tp, real, seq, blk);
 }
 
-// Forward launch that also writes the adjoint's checkpoints (complex64 storage).
-template <int NP>
-__global__ void __launch_bounds__(chain_max_threads(NP, false), chain_min_ctas(NP, false))
+// Forward launch that also writes the adjoint's checkpoints (complex64 storage), for the
+// Manakov or the per-polarization NLPR.
+template <int NP, bool PERPOL = false>
+__global__ void __launch_bounds__(chain_max_threads(NP, PERPOL), chain_min_ctas(NP, PERPOL))
     cbessfm_fwd_ckpt_kernel(const ChainArgs a) {
-    constexpr int E = chain_slots(NP, false);
+    constexpr int E = chain_slots(NP, PERPOL);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kMaxG];
     __shared__ float2 s_rot[kRotTable];
@@ -752,8 +753,8 @@ __global__ void __launch_bounds__(chain_max_threads(NP, false), chain_min_ctas(N
     const bool real = item < total;
     const int seq = real ? (int)(item / a.n_blocks) : 0;
     const int blk = real ? (int)(item % a.n_blocks) : 0;
-    chain_block<NP, 0, true>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, s_tw, s_taps, tp,
-                             real, seq, blk);
+    chain_block<NP, 0, true, PERPOL>(a, smem, a.region_bytes, &bars[tp.g], 0u, s_rot, s_tw,
+                                     s_taps, tp, real, seq, blk);
 }
 
 // Persistent form for a batch of jobs that share N', the subband count and the storage type:

@@ -1,6 +1,7 @@
 """Per-polarization NLPR (cbessfm_set_nlpr_mode(plan, 1); Eqs. (NLPR_polx), (NLPR_poly)) on the
 GPU against the oracle's per-polarization chain, mode B: rel-L2 <= 1e-5 like the Manakov form.
-Switching back restores the Manakov result bit for bit; gradients refuse the mode."""
+Switching back restores the Manakov result bit for bit.  Its gradients are in
+test_gpu_adjoint_perpol.py."""
 import dataclasses
 
 import numpy as np
@@ -73,7 +74,7 @@ def test_per_pol_c2_size_sampled_blocks():
         assert rel_l2(got[b][sel], want[sel], f"perpol/c2/realization{b}") <= TOL
 
 
-def test_per_pol_in_a_batch_and_gradients_refuse_it():
+def test_per_pol_in_a_batch():
     import torch
     from paper_2409_14489_gb300 import cbessfm
     cases = [Case(3, 256, 16, 2, 5, 0.3, 5000, sample_rate=192e9, seed=3),
@@ -89,7 +90,3 @@ def test_per_pol_in_a_batch_and_gradients_refuse_it():
     torch.cuda.synchronize()
     for plan, x, y in jobs:
         assert torch.equal(y, plan.backpropagate(x))
-    plan0 = jobs[0][0]
-    ws = plan0.new_workspace(cases[0].L, 1)
-    with pytest.raises(cbessfm.CBESSFMError, match="Manakov"):
-        plan0.backpropagate_checkpointed(jobs[0][1], ws)
