@@ -131,12 +131,16 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
  * Differentiation form.  The paper fits its taps offline with finite-difference gradients
  * (Sec. III-B); these calls give the exact gradient of a real loss L with respect to every
  * step's taps, the splitting ratio and the input, so the taps and rho can be trained on the
- * device.  Gradient convention for complex data: G = dL/dRe + j dL/dIm, stored like the field.
- * complex64 storage only.
+ * device.  Gradient convention for complex data: G = dL/dRe + j dL/dIm, stored like a
+ * complex64 field.  Plans with 16-bit storage take and return their input and output fields in
+ * that storage; the checkpoints, grad_out and grad_in are complex64 for every storage type (the
+ * forward widens its input into the workspace and narrows its complex64 result into `out`, so
+ * the gradients are those of the chain at the storage-rounded input).
  *
  * cbessfm_grad_workspace_size -- bytes of device workspace (caller-allocated, 256-byte aligned)
  *   holding, per overlap-and-save block, n_steps + 2 checkpoints of the block's field, two
- *   block-sized scratch fields of the adjoint and the per-block partial gradients.
+ *   block-sized scratch fields of the adjoint and the per-block partial gradients, and for
+ *   16-bit plans two complex64 copies of the whole input/output.
  */
 cbessfm_status cbessfm_grad_workspace_size(const cbessfm_plan* plan, int64_t n_samples, int batch,
                                            size_t* bytes);
@@ -296,9 +300,12 @@ cbessfm_status cbessfm_backpropagate_host(cbessfm_plan* plan, const void* host_i
  * this form computes the same operator sequence with a different block decomposition, so the
  * two agree where both overlaps cover their memory.
  * cbessfm_streamed_workspace_size -- bytes of device workspace for the intermediate fields
- *   (0, 1 or 2 fields of n_samples * batch complex64 4D samples, each rounded up to 256 bytes).
- * cbessfm_backpropagate_streamed -- complex64 storage only; in, out and workspace must not
- *   overlap; asynchronous on `stream`.  With steps <= 1 it is cbessfm_backpropagate.
+ *   (0, 1 or 2 fields of n_samples * batch complex64 4D samples, each rounded up to 256 bytes;
+ *   2 for 16-bit plans from two steps on).
+ * cbessfm_backpropagate_streamed -- in, out and workspace must not overlap; asynchronous on
+ *   `stream`.  With steps <= 1 it is cbessfm_backpropagate.  The fields between passes are
+ *   complex64 for every storage type: a 16-bit plan's input is widened into the workspace
+ *   first and the last pass's result is narrowed (round to nearest) into `out`.
  */
 cbessfm_status cbessfm_streamed_workspace_size(const cbessfm_plan* plan, int64_t n_samples,
                                                int batch, size_t* bytes);

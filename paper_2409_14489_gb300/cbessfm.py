@@ -261,7 +261,7 @@ class Plan:
     def backpropagate_checkpointed(self, x, workspace, out=None, stream=None):
         """Forward chain that also stores the adjoint's checkpoints in ``workspace``."""
         import torch
-        batch, L = self._field(x, "x")          # the library refuses 16-bit storage here
+        batch, L = self._field(x, "x")          # the plan's storage; checkpoints are complex64
         if out is None:
             out = torch.empty_like(x)
         self._field(out, "out", like=x)
@@ -332,9 +332,10 @@ class Plan:
         return n.value
 
     def backpropagate_streamed(self, x, out=None, workspace=None, stream=None):
-        """Per-step streamed form (``cbessfm_backpropagate_streamed``); complex64 only."""
+        """Per-step streamed form (``cbessfm_backpropagate_streamed``); the fields between
+        passes are complex64 whatever the plan's storage."""
         import torch
-        batch, L = self._field(x, "x")          # the library refuses 16-bit storage here
+        batch, L = self._field(x, "x")
         if out is not None:
             self._field(out, "out", like=x)
         need = self.streamed_workspace_size(L, batch)

@@ -33,6 +33,7 @@
 #include "block_count.h"
 #include "adj_kernel.cuh"
 #include "internal.h"
+#include "storage_convert.h"
 
 namespace cbessfm {
 
@@ -142,9 +143,9 @@ int adj_region_bytes(const PlanImpl& p) {
 }
 
 // Workspace: checkpoints | adjoint scratch (two fields per block) | per-block partial
-// gradients | FP64 sums.
+// gradients | FP64 sums | for 16-bit plans, complex64 copies of the forward's input and output.
 struct Layout {
-    size_t ckpt_bytes, stash_bytes, part_bytes, padded_bytes, total;
+    size_t ckpt_bytes, stash_bytes, part_bytes, padded_bytes, conv_bytes, total;
     long long n_blk;
     int part_stride;
 };
@@ -163,7 +164,9 @@ Layout layout(const PlanImpl& p, long long n_samples, int batch) {
     l.ckpt_bytes = (l.ckpt_bytes + 255) / 256 * 256;
     l.stash_bytes = (l.stash_bytes + 255) / 256 * 256;
     l.part_bytes = (l.part_bytes + 255) / 256 * 256;
-    l.total = l.ckpt_bytes + l.stash_bytes + l.part_bytes + l.padded_bytes;
+    l.conv_bytes = p.storage != CBESSFM_C64
+                       ? 2 * (((size_t)n_samples * batch * 16 + 255) / 256 * 256) : 0;
+    l.total = l.ckpt_bytes + l.stash_bytes + l.part_bytes + l.padded_bytes + l.conv_bytes;
     return l;
 }
 
@@ -171,8 +174,6 @@ cbessfm_status check_common(const cbessfm_plan* plan, int64_t n_samples, int bat
                             const void* workspace, size_t ws_bytes, const PlanImpl** pp) {
     const PlanImpl* p = plan_impl(plan);
     if (p == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
-    if (p->storage != CBESSFM_C64)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "gradients need complex64 storage");
     if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
     if (too_many_blocks(blocks_for(n_samples, p->V), batch))
         return fail(CBESSFM_ERR_UNSUPPORTED, "too many blocks");
@@ -218,18 +219,36 @@ cbessfm_status cbessfm_backpropagate_checkpointed(const cbessfm_plan* plan, cons
     if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
     if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u)
         return fail(CBESSFM_ERR_INVALID_ARG, "in/out must be 16-byte aligned");
-    const unsigned long long bytes = (unsigned long long)n_samples * batch * 16ull;
+    const bool wide = p->storage != CBESSFM_C64;  // 16-bit fields around the complex64 chain
+    const unsigned long long bytes = (unsigned long long)n_samples * batch * (wide ? 8ull : 16ull);
     const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
     if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
+    const uintptr_t w0 = reinterpret_cast<uintptr_t>(workspace), w1 = w0 + ws_bytes;
+    if ((i0 < w1 && w0 < i0 + bytes) || (o0 < w1 && w0 < o0 + bytes))
+        return fail(CBESSFM_ERR_ALIAS, "workspace overlaps in or out");
+    const cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+    const Layout l = layout(*p, n_samples, batch);
+    unsigned char* conv = static_cast<unsigned char*>(workspace) + l.total - l.conv_bytes;
+    float4* const in64 = reinterpret_cast<float4*>(conv);
+    float4* const out64 = reinterpret_cast<float4*>(conv + l.conv_bytes / 2);
+    const long long n_all = (long long)n_samples * batch;
+    if (wide) {
+        const cudaError_t e = launch_widen(p->storage, in, in64, n_all, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward input widening");
+    }
     ChainArgs a = make_chain_args(*p);
-    a.in = in;
-    a.out = out;
+    a.in = wide ? static_cast<const void*>(in64) : in;
+    a.out = wide ? static_cast<void*>(out64) : out;
     a.L = n_samples;
     a.batch = batch;
     a.n_blocks = (int)blocks_for(n_samples, p->V);
     a.ckpt = static_cast<float2*>(workspace);
-    const cudaError_t e = dispatch<false>(p->n_fft, a, p->threads, reinterpret_cast<cudaStream_t>(stream));
+    cudaError_t e = dispatch<false>(p->n_fft, a, p->threads, cs);
     if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward launch");
+    if (wide) {
+        e = launch_narrow(p->storage, out64, out, n_all, cs);
+        if (e != cudaSuccess) return cuda_fail(e, "checkpointed forward output narrowing");
+    }
     return CBESSFM_OK;
 }
 

@@ -14,6 +14,7 @@
 #include "abi_guard.h"
 #include "block_count.h"
 #include "internal.h"
+#include "storage_convert.h"
 
 
 namespace cbessfm {
@@ -487,6 +488,8 @@ static cbessfm_status plan_create_body(const cbessfm_link* link, int bands, int 
     CB_TRY(launch_build_gvd(p, nullptr), "build GVD tables");
     CB_TRY(launch_transpose_taps(p, nullptr), "transpose taps");
     CB_TRY(prepare_forward(n_fft, (int)storage, kMaxDynSmem), "set shared-memory limit");
+    if (storage != CBESSFM_C64)      // the streamed passes of a 16-bit plan run complex64 kernels
+        CB_TRY(prepare_forward(n_fft, (int)CBESSFM_C64, kMaxDynSmem), "set shared-memory limit");
     CB_TRY(cudaDeviceSynchronize(), "plan tables");
 #undef CB_TRY
 
@@ -572,7 +575,13 @@ cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, v
 // workspace's two buffers.
 namespace {
 
-size_t streamed_buffers(const PlanImpl& p) { return p.n_st >= 3 ? 2 : (p.n_st == 2 ? 1 : 0); }
+// complex64 fields of the streamed form's workspace: ping-pong between passes (one for two
+// steps); a 16-bit plan's passes start from a widened copy of the input and end in a field
+// that is narrowed into the output, which takes both fields from two steps on.
+size_t streamed_buffers(const PlanImpl& p) {
+    if (p.storage != CBESSFM_C64) return p.n_st >= 2 ? 2 : 0;
+    return p.n_st >= 3 ? 2 : (p.n_st == 2 ? 1 : 0);
+}
 
 }  // namespace
 
@@ -594,8 +603,6 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
     clear_error();
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     const PlanImpl& p = plan->impl;
-    if (p.storage != CBESSFM_C64)
-        return fail(CBESSFM_ERR_UNSUPPORTED, "the streamed form needs complex64 storage");
     if (p.n_st <= 1) return cbessfm_backpropagate(plan, in, out, n_samples, batch, stream);
     if (in == nullptr || out == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "in/out is NULL");
     if (n_samples < 1 || batch < 1) return fail(CBESSFM_ERR_INVALID_ARG, "n_samples and batch must be >= 1");
@@ -609,7 +616,8 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
     if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) |
          reinterpret_cast<uintptr_t>(workspace)) & 15u)
         return fail(CBESSFM_ERR_INVALID_ARG, "in/out/workspace must be 16-byte aligned");
-    const unsigned long long bytes = (unsigned long long)n_samples * batch * 16ull;
+    const bool wide = p.storage != CBESSFM_C64;   // 16-bit fields around complex64 passes
+    const unsigned long long bytes = (unsigned long long)n_samples * batch * (wide ? 8ull : 16ull);
     const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), o0 = reinterpret_cast<uintptr_t>(out);
     const uintptr_t w0 = reinterpret_cast<uintptr_t>(workspace), w1 = w0 + streamed_buffers(p) * one;
     if (i0 < o0 + bytes && o0 < i0 + bytes) return fail(CBESSFM_ERR_ALIAS, "out overlaps in");
@@ -618,10 +626,20 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
     unsigned char* buf[2] = {static_cast<unsigned char*>(workspace),
                              static_cast<unsigned char*>(workspace) + one};
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const long long n_all = (long long)n_samples * batch;
+    if (wide) {                                   // widened input in buf[1]; pass s writes buf[s & 1]
+        const cudaError_t e = launch_widen(p.storage, in, reinterpret_cast<float4*>(buf[1]), n_all, st);
+        if (e != cudaSuccess) return cuda_fail(e, "streamed input widening");
+    }
     for (int s = 0; s < p.n_st; ++s) {
         ChainArgs a = make_chain_args(p);
-        a.in = s == 0 ? in : buf[(s - 1) & 1];
-        a.out = s == p.n_st - 1 ? out : buf[s & 1];
+        if (wide) {
+            a.in = s == 0 ? buf[1] : buf[(s - 1) & 1];
+            a.out = buf[s & 1];
+        } else {
+            a.in = s == 0 ? in : buf[(s - 1) & 1];
+            a.out = s == p.n_st - 1 ? out : buf[s & 1];
+        }
         a.L = n_samples;
         a.batch = batch;
         a.n_blocks = (int)n_blocks;
@@ -630,8 +648,13 @@ cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const vo
         const size_t half = (size_t)(p.N / 2 + 1);
         a.gvd_first = p.d_gvd_half + (s == 0 ? 0 : 3) * half;
         a.gvd_last = p.d_gvd_half + (s == p.n_st - 1 ? 2 : 1) * half;
-        const cudaError_t e = launch_forward(p, a, st);
+        const cudaError_t e = wide ? launch_forward_c64(p, a, st) : launch_forward(p, a, st);
         if (e != cudaSuccess) return cuda_fail(e, "streamed pass launch");
+    }
+    if (wide) {
+        const cudaError_t e = launch_narrow(p.storage, reinterpret_cast<const float4*>(buf[(p.n_st - 1) & 1]),
+                                            out, n_all, st);
+        if (e != cudaSuccess) return cuda_fail(e, "streamed output narrowing");
     }
     return CBESSFM_OK;
 }

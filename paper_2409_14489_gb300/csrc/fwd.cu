@@ -1,6 +1,7 @@
 // fwd.cu -- FP64 GVD table builder and dispatch of the forward chain kernel instantiations.
 #include "device_common.cuh"
 #include "internal.h"
+#include "storage_convert.h"
 #include "fwd_launch.h"
 
 namespace cbessfm {
@@ -170,6 +171,10 @@ cudaError_t prepare_forward(int np, int storage, int smem_bytes) {
         case 2: return prepare_st<2>(np, smem_bytes);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_forward_c64(const PlanImpl& p, const ChainArgs& a, cudaStream_t stream) {
+    return launch_st<0>(p.n_fft, a, p.threads, stream);
 }
 
 cudaError_t launch_forward(const PlanImpl& p, const ChainArgs& a, cudaStream_t stream) {
