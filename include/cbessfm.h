@@ -201,8 +201,11 @@ cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_
 
 /*
  * cbessfm_batch_run -- process every job: one counter reset and one persistent kernel per group,
- * asynchronous on `stream`.  It issues no host synchronization and no allocation, so it can be
- * captured into a CUDA graph and replayed.
+ * asynchronous on `stream`.  The groups after the first run on streams the batch owns, forked
+ * from `stream` and joined back into it by events, so one group's CTAs take over the SMs that
+ * another group's finished CTAs free; the call returns with all of them ordered before later
+ * work on `stream`.  It issues no host synchronization and no allocation, so it can be captured
+ * into a CUDA graph and replayed.
  */
 cbessfm_status cbessfm_batch_run(const cbessfm_batch* batch, cbessfm_stream stream);
 

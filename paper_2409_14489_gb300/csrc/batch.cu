@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <new>
 #include <tuple>
@@ -27,6 +29,12 @@ struct cbessfm_batch {
         int item_off = 0, n_items = 0;
     };
     std::vector<Group> groups;
+    // groups after the first run on their own streams, forked from and joined back into the
+    // caller's stream, so one group's persistent CTAs take over the SMs that another group's
+    // finished CTAs free (empty with CBESSFM_BATCH_SERIAL=1: one group after the other)
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
     cbessfm::ChainArgs* d_jobs = nullptr;
     int2* d_items = nullptr;
     unsigned int* d_counters = nullptr;
@@ -39,6 +47,11 @@ namespace {
 
 void free_batch(cbessfm_batch* b) {
     if (!b) return;
+    for (cudaStream_t st : b->side)
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : b->joins)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     cudaFree(b->d_jobs);
     cudaFree(b->d_items);
     cudaFree(b->d_counters);
@@ -168,6 +181,18 @@ static cbessfm_status batch_create_body(const cbessfm_job* jobs, int njobs, cbes
         e = cudaMemcpy(b->d_jobs, args.data(), sizeof(ChainArgs) * args.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !items.empty())
         e = cudaMemcpy(b->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice);
+    const char* serial = std::getenv("CBESSFM_BATCH_SERIAL");
+    if (e == cudaSuccess && b->groups.size() > 1 && !(serial && std::strcmp(serial, "1") == 0)) {
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; ++k) {
+            cudaStream_t st = nullptr;
+            cudaEvent_t ev = nullptr;
+            e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+            if (e == cudaSuccess) b->side.push_back(st);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) b->joins.push_back(ev);
+        }
+    }
     if (e != cudaSuccess) {
         free_batch(b);
         return cuda_fail(e, "batch descriptors");
@@ -185,16 +210,25 @@ cbessfm_status cbessfm_batch_run(const cbessfm_batch* b, cbessfm_stream stream) 
     clear_error();
     if (b == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "batch is NULL");
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    const bool fan = !b->side.empty();
+    // every group's work counter reset first, on the caller's stream
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned int) * b->groups.size(), st);
+    if (e == cudaSuccess && fan) e = cudaEventRecord(b->fork, st);
+    for (size_t k = 1; fan && k < b->groups.size() && e == cudaSuccess; ++k)
+        e = cudaStreamWaitEvent(b->side[k - 1], b->fork, 0);
+    for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
         const cbessfm_batch::Group& gr = b->groups[gi];
-        cudaError_t e = cudaMemsetAsync(b->d_counters + gi, 0, sizeof(unsigned int), st);
-        if (e == cudaSuccess)
-            e = launch_forward_persistent(gr.np, gr.storage, b->d_jobs, b->d_items + gr.item_off,
-                                          gr.n_items, b->d_counters + gi, gr.n_sb, gr.G,
-                                          gr.region_bytes, gr.tbl_bytes, gr.per_pol, gr.threads,
-                                          gr.grid, st);
-        if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+        const cudaStream_t gs = (fan && gi > 0) ? b->side[gi - 1] : st;
+        e = launch_forward_persistent(gr.np, gr.storage, b->d_jobs, b->d_items + gr.item_off,
+                                      gr.n_items, b->d_counters + gi, gr.n_sb, gr.G,
+                                      gr.region_bytes, gr.tbl_bytes, gr.per_pol, gr.threads,
+                                      gr.grid, gs);
     }
+    for (size_t k = 1; fan && k < b->groups.size() && e == cudaSuccess; ++k) {
+        e = cudaEventRecord(b->joins[k - 1], b->side[k - 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->joins[k - 1], 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     return CBESSFM_OK;
 }
 
