@@ -2,13 +2,15 @@
 //
 // A receiver's samples usually arrive in host memory.  cbessfm_backpropagate_host copies the
 // batch in by groups of realizations on one copy stream, runs the chain kernel in launches of
-// whole waves of OLS blocks on the caller's stream, and copies each group out on a second copy
+// whole waves of OLS blocks on the caller's stream and a second compute stream, and copies each
+// group out on a second copy
 // stream as soon as the launches holding its last block have finished.  A launch waits only for
-// the copies of the realizations its blocks read, so the time approaches the larger of the
+// the copies of the realizations its blocks read, and consecutive launches alternate between two
+// compute streams so a launch's last wave overlaps the next; the time approaches the larger of the
 // kernel time and the transfer time plus one group's copy in and out.  Launches are cut at
 // multiples of the device's resident blocks (one wave of CTAs), not at realization boundaries:
-// a launch of one realization's blocks would leave most SMs idle in its last wave.  The copy
-// streams and events belong to the plan and are created at the first call.
+// a launch of one realization's blocks would leave most SMs idle in its last wave.  The copy and
+// compute streams and the events belong to the plan and are created at the first call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -29,7 +31,9 @@ constexpr int kMaxCopyGroups = 64;
 struct HostPipeline {
     std::mutex mu;                    // one pipelined call per plan at a time
     cudaStream_t h2d = nullptr, d2h = nullptr;
-    cudaEvent_t start = nullptr, end = nullptr, computed = nullptr;
+    cudaStream_t comp2 = nullptr;     // second compute stream: consecutive launches alternate
+    cudaEvent_t start = nullptr, end = nullptr;
+    cudaEvent_t launched[2] = {};     // after the latest launch on the caller's stream / comp2
     cudaEvent_t copied[kMaxCopyGroups] = {};
     int n_sm = 0;                     // SM count of the plan's device
 };
@@ -38,9 +42,11 @@ void destroy_host_pipeline(HostPipeline* hp) {
     if (hp == nullptr) return;
     if (hp->h2d) cudaStreamDestroy(hp->h2d);
     if (hp->d2h) cudaStreamDestroy(hp->d2h);
+    if (hp->comp2) cudaStreamDestroy(hp->comp2);
+    for (int k = 0; k < 2; ++k)
+        if (hp->launched[k]) cudaEventDestroy(hp->launched[k]);
     if (hp->start) cudaEventDestroy(hp->start);
     if (hp->end) cudaEventDestroy(hp->end);
-    if (hp->computed) cudaEventDestroy(hp->computed);
     for (int k = 0; k < kMaxCopyGroups; ++k)
         if (hp->copied[k]) cudaEventDestroy(hp->copied[k]);
     delete hp;
@@ -55,9 +61,11 @@ cudaError_t create_pipeline(HostPipeline* hp, int device) {
     cudaError_t e = cudaDeviceGetAttribute(&hp->n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->h2d, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->d2h, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->comp2, cudaStreamNonBlocking);
+    for (int k = 0; e == cudaSuccess && k < 2; ++k)
+        e = cudaEventCreateWithFlags(&hp->launched[k], flags);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->start, flags);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->end, flags);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->computed, flags);
     for (int k = 0; e == cudaSuccess && k < kMaxCopyGroups; ++k)
         e = cudaEventCreateWithFlags(&hp->copied[k], flags);
     return e;
@@ -127,10 +135,17 @@ static cbessfm_status backpropagate_host_body(cbessfm_plan* plan, const void* ho
     const int cg = (batch + kMaxCopyGroups - 1) / kMaxCopyGroups;
     const int n_groups = (batch + cg - 1) / cg;
 
+    // consecutive launches alternate between the caller's stream and the pipeline's second
+    // compute stream, so a launch's last partial wave overlaps the next launch instead of
+    // draining the GPU (they write disjoint blocks); CBESSFM_PIPELINE_STREAMS=1 keeps one stream
+    int n_comp = 2;
+    if (const char* env = std::getenv("CBESSFM_PIPELINE_STREAMS")) n_comp = std::atoi(env) == 1 ? 1 : 2;
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const cudaStream_t comp[2] = {st, hp.comp2};
     cudaError_t e = cudaEventRecord(hp.start, st);              // after the caller's earlier work
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.h2d, hp.start, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.d2h, hp.start, 0);
+    if (e == cudaSuccess && n_comp == 2) e = cudaStreamWaitEvent(hp.comp2, hp.start, 0);
     if (e != cudaSuccess) return cuda_fail(e, "pipeline start");
     const unsigned char* hin = static_cast<const unsigned char*>(host_in);
     unsigned char* hout = static_cast<unsigned char*>(host_out);
@@ -149,19 +164,25 @@ static cbessfm_status backpropagate_host_body(cbessfm_plan* plan, const void* ho
         if (e == cudaSuccess) e = cudaEventRecord(hp.copied[g], hp.h2d);
         if (e != cudaSuccess) return cuda_fail(e, "pipeline copy in");
     }
-    int waited = -1, out_next = 0;                              // groups waited for / copied out
-    for (int c0 = 0; c0 < n_ctas;) {
+    int waited[2] = {-1, -1}, out_next = 0;     // groups waited for per compute stream / copied out
+    bool used2 = false;
+    for (int c0 = 0, li = 0; c0 < n_ctas; ++li) {
         const int want = c0 == 0 ? first_launch : per_launch;
         const int nc = n_ctas - c0 > want ? want : n_ctas - c0;
         const int i1 = (c0 + nc) * p.G < total ? (c0 + nc) * p.G : total;   // items [c0 G, i1)
         const int g_in = (int)((i1 - 1) / n_blocks) / cg;       // last group the launch reads
-        if (g_in > waited) {
-            e = cudaStreamWaitEvent(st, hp.copied[g_in], 0);
+        const int cs = n_comp == 2 ? (li & 1) : 0;
+        used2 = used2 || cs == 1;
+        if (g_in > waited[cs]) {
+            e = cudaStreamWaitEvent(comp[cs], hp.copied[g_in], 0);
             if (e != cudaSuccess) return cuda_fail(e, "pipeline wait for copy in");
-            waited = g_in;
+            waited[cs] = g_in;
         }
-        const cbessfm_status s = forward_range(plan, din, dout, n_samples, batch, c0, nc, stream);
+        const cbessfm_status s = forward_range(plan, din, dout, n_samples, batch, c0, nc,
+                                               reinterpret_cast<cbessfm_stream>(comp[cs]));
         if (s != CBESSFM_OK) return s;
+        e = cudaEventRecord(hp.launched[cs], comp[cs]);
+        if (e != cudaSuccess) return cuda_fail(e, "pipeline launch event");
         // groups whose every block is now computed go out in one copy
         int g_end = out_next;
         while (g_end < n_groups) {
@@ -174,9 +195,10 @@ static cbessfm_status backpropagate_host_body(cbessfm_plan* plan, const void* ho
             size_t off0, b0, off1, b1;
             group_span(out_next, &off0, &b0);
             group_span(g_end - 1, &off1, &b1);
-            // the wait binds to this record; later records of the event do not affect it
-            e = cudaEventRecord(hp.computed, st);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(hp.d2h, hp.computed, 0);
+            // every launch so far is complete once the latest launch on each compute stream is
+            // (each stream runs its own launches in order); a wait binds to the current record
+            e = cudaStreamWaitEvent(hp.d2h, hp.launched[0], 0);
+            if (e == cudaSuccess && used2) e = cudaStreamWaitEvent(hp.d2h, hp.launched[1], 0);
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(hout + off0, dout + off0, off1 + b1 - off0,
                                     cudaMemcpyDeviceToHost, hp.d2h);
