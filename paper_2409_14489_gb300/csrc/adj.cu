@@ -33,6 +33,7 @@
 #include "block_count.h"
 #include "adj_kernel.cuh"
 #include "internal.h"
+#include "trace.h"
 #include "storage_convert.h"
 
 namespace cbessfm {
@@ -212,6 +213,7 @@ cbessfm_status cbessfm_grad_workspace_size(const cbessfm_plan* plan, int64_t n_s
 cbessfm_status cbessfm_backpropagate_checkpointed(const cbessfm_plan* plan, const void* in, void* out,
                                                   int64_t n_samples, int batch, void* workspace,
                                                   size_t ws_bytes, cbessfm_stream stream) {
+    TraceRange trace_range("cbessfm:backpropagate_checkpointed");
     clear_error();
     const PlanImpl* p = nullptr;
     cbessfm_status st = check_common(plan, n_samples, batch, workspace, ws_bytes, &p);
@@ -255,6 +257,7 @@ cbessfm_status cbessfm_backpropagate_checkpointed(const cbessfm_plan* plan, cons
 cbessfm_status cbessfm_grad(const cbessfm_plan* plan, const void* grad_out, double* grad_coeffs,
                             double* grad_ratio, void* grad_in, void* workspace, size_t ws_bytes,
                             int64_t n_samples, int batch, cbessfm_stream stream) {
+    TraceRange trace_range("cbessfm:grad");
     clear_error();
     const PlanImpl* p = nullptr;
     cbessfm_status st = check_common(plan, n_samples, batch, workspace, ws_bytes, &p);

@@ -14,6 +14,7 @@
 #include "abi_guard.h"
 #include "block_count.h"
 #include "internal.h"
+#include "trace.h"
 #include "storage_convert.h"
 
 
@@ -506,6 +507,7 @@ static cbessfm_status plan_create_body(const cbessfm_link* link, int bands, int 
 cbessfm_status cbessfm_plan_create(const cbessfm_link* link, int bands, int steps, double ratio,
                                    const float* coeffs, int ntaps, int n_fft, int overlap,
                                    cbessfm_storage storage, cbessfm_plan** out) {
+    TraceRange trace_range("cbessfm:plan_create");
     clear_error();
     return abi_guard([&] {
         return plan_create_body(link, bands, steps, ratio, coeffs, ntaps, n_fft, overlap, storage,
@@ -549,11 +551,13 @@ static cbessfm_status set_coeffs_body(cbessfm_plan* plan, const float* coeffs, i
 
 cbessfm_status cbessfm_set_coeffs(cbessfm_plan* plan, const float* coeffs, int on_device,
                                   cbessfm_stream stream) {
+    TraceRange trace_range("cbessfm:set_coeffs");
     clear_error();
     return abi_guard([&] { return set_coeffs_body(plan, coeffs, on_device, stream); });
 }
 
 cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_stream stream) {
+    TraceRange trace_range("cbessfm:set_ratio");
     clear_error();
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     if (!(ratio >= 0.0 && ratio <= 1.0)) return fail(CBESSFM_ERR_INVALID_ARG, "ratio must be in [0, 1]");
@@ -565,6 +569,7 @@ cbessfm_status cbessfm_set_ratio(cbessfm_plan* plan, double ratio, cbessfm_strea
 
 cbessfm_status cbessfm_backpropagate(const cbessfm_plan* plan, const void* in, void* out,
                                      int64_t n_samples, int batch, cbessfm_stream stream) {
+    TraceRange trace_range("cbessfm:backpropagate");
     clear_error();
     return forward_range(plan, in, out, n_samples, batch, 0, 0, stream);
 }
@@ -600,6 +605,7 @@ cbessfm_status cbessfm_streamed_workspace_size(const cbessfm_plan* plan, int64_t
 cbessfm_status cbessfm_backpropagate_streamed(const cbessfm_plan* plan, const void* in, void* out,
                                               void* workspace, size_t ws_bytes, int64_t n_samples,
                                               int batch, cbessfm_stream stream) {
+    TraceRange trace_range("cbessfm:backpropagate_streamed");
     clear_error();
     if (plan == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "plan is NULL");
     const PlanImpl& p = plan->impl;

@@ -21,6 +21,7 @@
 #include "block_count.h"
 #include "device_common.cuh"
 #include "internal.h"
+#include "trace.h"
 
 struct cbessfm_batch {
     struct Group {
@@ -202,11 +203,13 @@ static cbessfm_status batch_create_body(const cbessfm_job* jobs, int njobs, cbes
 }
 
 cbessfm_status cbessfm_batch_create(const cbessfm_job* jobs, int njobs, cbessfm_batch** out) {
+    TraceRange trace_range("cbessfm:batch_create");
     clear_error();
     return abi_guard([&] { return batch_create_body(jobs, njobs, out); });
 }
 
 cbessfm_status cbessfm_batch_run(const cbessfm_batch* b, cbessfm_stream stream) {
+    TraceRange trace_range("cbessfm:batch_run");
     clear_error();
     if (b == nullptr) return fail(CBESSFM_ERR_INVALID_ARG, "batch is NULL");
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -17,6 +17,7 @@
 
 #include "abi_guard.h"
 #include "internal.h"
+#include "trace.h"
 
 namespace cbessfm {
 namespace {
@@ -155,6 +156,7 @@ static cbessfm_status analytic_taps_body(const cbessfm_link* link, int bands, in
 cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int steps,
                                      int spans_per_step, const double* step_power, int ntaps,
                                      int grid, double* taps, double* response) {
+    TraceRange trace_range("cbessfm:analytic_taps");
     clear_error();
     return abi_guard([&] {
         return analytic_taps_body(link, bands, steps, spans_per_step, step_power, ntaps, grid,

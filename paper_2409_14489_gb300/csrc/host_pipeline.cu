@@ -23,6 +23,7 @@
 #include "block_count.h"
 #include "device_common.cuh"
 #include "internal.h"
+#include "trace.h"
 
 namespace cbessfm {
 
@@ -216,6 +217,7 @@ static cbessfm_status backpropagate_host_body(cbessfm_plan* plan, const void* ho
 cbessfm_status cbessfm_backpropagate_host(cbessfm_plan* plan, const void* host_in, void* host_out,
                                           void* dev_in, void* dev_out, int64_t n_samples,
                                           int batch, int launch_blocks, cbessfm_stream stream) {
+    TraceRange trace_range("cbessfm:backpropagate_host");
     clear_error();
     // the pipeline's mutexes are the one thing here that can throw
     return abi_guard([&] {

@@ -18,6 +18,12 @@ def is_distributed() -> bool:
     return dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1
 
 
+def rank() -> int:
+    """This process's rank (0 without a process group)."""
+    import torch.distributed as dist
+    return dist.get_rank() if dist.is_available() and dist.is_initialized() else 0
+
+
 def _device():
     import torch.distributed as dist
     return torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl" \
