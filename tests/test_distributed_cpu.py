@@ -105,3 +105,57 @@ def test_shard_edge_cases_and_single_process_fallbacks():
     p.grad = torch.full((2,), 0.5)
     distributed.average_gradients_([p])
     assert torch.equal(p.grad, torch.full((2,), 0.5))
+
+
+class _InjectedFailure(RuntimeError):
+    pass
+
+
+def _failing_worker(rank, world, port, q):
+    """Rank 1's loss raises in its 4th iteration (before that iteration's gradient all-reduce);
+    rank 0 must see an error from its next collective instead of waiting forever."""
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    from paper_2409_14489_gb300 import train
+    model = _StandIn()
+    x, target = _data(rank, 4)
+    calls = [0]
+
+    def loss_fn(y):
+        calls[0] += 1
+        if rank == 1 and calls[0] == 4:
+            raise _InjectedFailure("injected failure on rank 1")
+        return torch.mean((y - target) ** 2)
+
+    try:
+        train.adam_fit(model, x, loss_fn, iters=30, lr_taps=0.05, lr_ratio=0.02)
+        q.put((rank, "finished", calls[0]))
+    except Exception as e:                      # noqa: BLE001 -- reported to the test
+        q.put((rank, type(e).__name__, calls[0]))
+    # no destroy_process_group: a failed rank just leaves, as a crashed one would
+
+
+def test_a_failed_rank_ends_the_others_collective_with_an_error():
+    """Failure detection on the host: one rank of a data-parallel training run fails between
+    steps; the survivor's next gradient all-reduce ends with an error (peer gone or the process
+    group's 20 s timeout) rather than hanging, and it had not taken another step."""
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_failing_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    try:
+        res = {r: (status, n) for r, status, n in (q.get(timeout=120) for _ in range(world))}
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert res[1] == ("_InjectedFailure", 4)
+    status0, calls0 = res[0]
+    assert status0 != "finished", res
+    assert calls0 == 4                          # its 4th step's all-reduce is where it stopped
