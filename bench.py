@@ -519,8 +519,8 @@ def run_gpu(args, wl, taps):
 
     # ---- end to end: pinned host buffers, H2D + launch + D2H inside the timed region ------
     # through cbessfm_backpropagate_host: copies in by realization on one stream, the chain
-    # kernel in launches of one (the first) or two waves of blocks, copies out on another stream
-    # as realizations complete; every step moves the whole batch in and out
+    # kernel in launches of one CTA per SM alternating between two compute streams, copies out
+    # on another stream as realizations complete; every step moves the whole batch in and out
     h_in = torch.from_numpy(fields).pin_memory()
     h_out = torch.empty_like(h_in).pin_memory()
     e2e_steps = max(3, min(args.steps, 10))
@@ -642,7 +642,7 @@ def run_gpu(args, wl, taps):
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": cpu_cores, "kind": "oracle",
                              "sample": cpu_desc, "single_core_value": cpu_single},
             "e2e": {"value": world * sym_per_step * e2e_steps / (e2e_ms / 1e3), "unit": UNIT,
-                    "api": "cbessfm_backpropagate_host (pinned host buffers; launches of one, then two waves of blocks)",
+                    "api": "cbessfm_backpropagate_host (pinned host buffers; launches of one CTA per SM on two alternating compute streams)",
                     "sequential_value": world * sym_per_step * e2e_steps / (e2e_seq_ms / 1e3),
                     "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
                     "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},

@@ -269,19 +269,20 @@ cbessfm_status cbessfm_analytic_taps(const cbessfm_link* link, int bands, int st
 /*
  * cbessfm_backpropagate_host -- cbessfm_backpropagate of fields in host memory, with the
  * transfers overlapped.  The batch is copied into `dev_in` in groups of realizations (at most 64
- * groups) on a host-to-device stream; the chain kernel runs on `stream` in launches of
+ * groups) on a host-to-device stream; the chain kernel runs in launches of
  * `launch_blocks` OLS blocks of the flattened (realization, block) list, each launch waiting
  * only for the groups it reads; each group is copied from `dev_out` to `host_out` on a
- * device-to-host stream once its last block is computed.  Both copy streams are owned by the
- * plan (created at the first call).  The paper has no counterpart; the chain and its result are
+ * device-to-host stream once its last block is computed.  The copy streams and the second
+ * compute stream are owned by the plan (created at the first call).  The paper has no counterpart; the chain and its result are
  * those of cbessfm_backpropagate, bit for bit.
  *   host_in, host_out  [batch][n_samples] samples in the plan's storage type; page-locked
  *                      memory (cudaHostAlloc / pinned tensors) lets the copies overlap.
  *   dev_in, dev_out    device buffers of the same size (caller-owned, must not overlap).
  *   launch_blocks      OLS blocks per launch, rounded up to whole CTAs of the plan; 0 = one
- *                      wave (the device's SM count times the CTAs resident per SM) for the
- *                      first launch and two waves for the later ones, which keeps every launch's
- *                      last wave full.
+ *                      CTA per SM per launch, the launches alternating between `stream` and a
+ *                      second compute stream owned by the plan so that two are in flight
+ *                      (with CBESSFM_PIPELINE_STREAMS=1 in the environment: all launches on
+ *                      `stream`, one wave of resident CTAs first and two waves after).
  * Asynchronous: completion is ordered on `stream` (synchronize it before reading host_out).
  * Calls on one plan are serialized on the host; concurrent calls with one plan wait for each
  * other's enqueueing, not for the device.  Errors: CBESSFM_ERR_INVALID_ARG for NULL buffers,

@@ -123,24 +123,30 @@ static cbessfm_status backpropagate_host_body(cbessfm_plan* plan, const void* ho
                                           chain_min_ctas(p.n_fft, p.per_pol != 0)) /
                           p.G);
     if (wave < 1) wave = 1;
-    // automatic sizing: one wave first (it waits only for the copies of the blocks it reads),
-    // then two waves per launch (fewer launch boundaries, each of which drains the GPU; on the
-    // c2 workload 1, 2, 3 waves gave 1.217, 1.204, 1.235 ms per step, everything after the first
-    // wave in one launch 1.669 ms); CBESSFM_PIPELINE_WAVES overrides the later count (tuning)
-    int later_waves = 2;
-    if (const char* env = std::getenv("CBESSFM_PIPELINE_WAVES")) later_waves = std::max(1, std::atoi(env));
-    const int first_launch = launch_blocks > 0 ? (launch_blocks + p.G - 1) / p.G : wave;
-    const int per_launch = launch_blocks > 0 ? first_launch : later_waves * wave;
-    const int n_ctas = (total + p.G - 1) / p.G;
-    // copy groups of `cg` realizations (at most kMaxCopyGroups groups)
-    const int cg = (batch + kMaxCopyGroups - 1) / kMaxCopyGroups;
-    const int n_groups = (batch + cg - 1) / cg;
-
     // consecutive launches alternate between the caller's stream and the pipeline's second
     // compute stream, so a launch's last partial wave overlaps the next launch instead of
     // draining the GPU (they write disjoint blocks); CBESSFM_PIPELINE_STREAMS=1 keeps one stream
     int n_comp = 2;
     if (const char* env = std::getenv("CBESSFM_PIPELINE_STREAMS")) n_comp = std::atoi(env) == 1 ? 1 : 2;
+    // automatic sizing. Two compute streams: launches of one CTA per SM each (half a wave at two
+    // resident CTAs per SM), so the two streams together keep one wave in flight and the copy
+    // out of each finished group starts early; on the c2 workload 76, 114, 152, 190, 228 CTAs
+    // per launch gave 1.557, 1.543, 1.176, 1.378, 1.261 ms per step (one stream with the sizing
+    // below: 1.300 ms on the same GPU). One stream: one wave first (it waits only for the copies
+    // of the blocks it reads), then two waves per launch (1, 2, 3 waves gave 1.217, 1.204,
+    // 1.235 ms, everything after the first wave in one launch 1.669 ms); CBESSFM_PIPELINE_WAVES
+    // overrides the later count (tuning)
+    int later_waves = 2;
+    if (const char* env = std::getenv("CBESSFM_PIPELINE_WAVES")) later_waves = std::max(1, std::atoi(env));
+    const int auto_first = n_comp == 2 ? hp.n_sm : wave;
+    const int auto_later = n_comp == 2 ? hp.n_sm : later_waves * wave;
+    const int first_launch = launch_blocks > 0 ? (launch_blocks + p.G - 1) / p.G : auto_first;
+    const int per_launch = launch_blocks > 0 ? first_launch : auto_later;
+    const int n_ctas = (total + p.G - 1) / p.G;
+    // copy groups of `cg` realizations (at most kMaxCopyGroups groups)
+    const int cg = (batch + kMaxCopyGroups - 1) / kMaxCopyGroups;
+    const int n_groups = (batch + cg - 1) / cg;
+
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const cudaStream_t comp[2] = {st, hp.comp2};
     cudaError_t e = cudaEventRecord(hp.start, st);              // after the caller's earlier work
