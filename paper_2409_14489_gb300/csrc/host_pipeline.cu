@@ -2,15 +2,15 @@
 //
 // A receiver's samples usually arrive in host memory.  cbessfm_backpropagate_host copies the
 // batch in by groups of realizations on one copy stream, runs the chain kernel in launches of
-// whole waves of OLS blocks on the caller's stream and a second compute stream, and copies each
-// group out on a second copy
-// stream as soon as the launches holding its last block have finished.  A launch waits only for
-// the copies of the realizations its blocks read, and consecutive launches alternate between two
-// compute streams so a launch's last wave overlaps the next; the time approaches the larger of the
-// kernel time and the transfer time plus one group's copy in and out.  Launches are cut at
-// multiples of the device's resident blocks (one wave of CTAs), not at realization boundaries:
-// a launch of one realization's blocks would leave most SMs idle in its last wave.  The copy and
-// compute streams and the events belong to the plan and are created at the first call.
+// OLS blocks that alternate between the caller's stream and a second compute stream, and copies
+// each group out on a second copy stream as soon as the launches holding its last block have
+// finished.  A launch waits only for the copies of the realizations its blocks read.  With two
+// compute streams each launch is one CTA per SM, so two launches together fill the GPU and the
+// last partial wave of one overlaps the next; with one stream, launches are whole waves of
+// resident CTAs.  Launches are cut at CTA counts, not at realization boundaries: a launch of one
+// realization's blocks would leave most SMs idle in its last wave.  The time approaches the
+// kernel time plus one group's copy in and out.  The copy and compute streams and the events
+// belong to the plan and are created at the first call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
