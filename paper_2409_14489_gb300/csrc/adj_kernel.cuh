@@ -497,7 +497,15 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     }
 
     // ---- 3. first GVD, adjoint of entry (MUX + IDFT_N), scatter to G_in ---------------------
-    atomicAdd(acc_rho, rho_part);                 // warps may span several small blocks
+    // the block's ratio sum: FP64 atomics on one shared word contend (a compare-and-swap per
+    // update), so when every warp lies within one block the warp first sums its lanes
+    if (TB % 32 == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rho_part += __shfl_xor_sync(0xffffffffu, rho_part, o);
+        if ((tp.tid & 31) == 0) atomicAdd(acc_rho, rho_part);
+    } else {
+        atomicAdd(acc_rho, rho_part);             // warps may span several small blocks
+    }
     {
         const float2* h = a.gvd + (size_t)gi * NP;
 #pragma unroll
