@@ -319,9 +319,11 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     // lanes 16 apart in the packed layout) and the slot reads are both conflict-free
     constexpr int CSH = 4;
     constexpr int CSL = NP + (NP >> CSH);              // float2 per (cos, sin) row
-    // DEMUX/MUX twiddles by one table value per polyphase row times a per-slot factor; 32 slots
-    // keep the plain table read: they leave no registers for the product
+    // DEMUX/MUX twiddles: 16 slots, one table value per polyphase row times a per-slot factor;
+    // 32 slots, one table value per thread and per-slot factors, the rows by powers (see below)
     constexpr bool kFactor = E == 16;
+    // 32-slot plans have at most 5 subbands (2 x 5 x N'/32 threads fill the CTA)
+    constexpr int kMaxBands32 = 5;
     const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
     unsigned char* region = smem + (size_t)g * region_bytes;
     // packed layout: the group arrays lie region_bytes / n_sb apart (at least XL float2; more when
@@ -462,19 +464,46 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         const float2* td = a.mix_td;                                    // [n_sb][E]
         int K0 = ci + j;
         K0 += (K0 < 0) ? N : 0;
+        if constexpr (kFactor) {
 #pragma unroll
-        for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
-        for (int r = 0; r < a.n_sb; ++r) {
-            const float2* er = eb + r * XLg;
-            const float2 w0 = __ldg(a.mix_tw + (size_t)r * N + K0);        // W_N^(K_0 r)
+            for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
+            for (int r = 0; r < a.n_sb; ++r) {
+                const float2* er = eb + r * XLg;
+                const float2 w0 = __ldg(a.mix_tw + (size_t)r * N + K0);    // W_N^(K_0 r)
+#pragma unroll
+                for (int t = 0; t < E; ++t) {
+                    const int kap = j + TPF * t;
+                    int K = ci + (kap < NP / 2 ? kap : kap - NP);
+                    K += (K < 0) ? N : 0;
+                    const float2 w = c_mul(w0, __ldg(td + r * E + t));
+                    x[t] = c_add(x[t], c_mul(er[2 * xpad_s<SH>(K & (NP - 1))], w));
+                }
+            }
+        } else {
+            // 32 slots: slot t outermost, so only the finished slots' sums stay live, and
+            // W_N^(K r) as the powers of W_N^K = W_N^(K_0) times slot t's row-1 factor: one
+            // table gather per thread instead of one per (r, t) (at most 4 products deep)
+            const float2 wk0 =
+                a.n_sb > 1 ? __ldg(a.mix_tw + (size_t)N + K0) : make_float2(1.f, 0.f);
 #pragma unroll
             for (int t = 0; t < E; ++t) {
                 const int kap = j + TPF * t;
                 int K = ci + (kap < NP / 2 ? kap : kap - NP);
                 K += (K < 0) ? N : 0;
-                const float2 w = kFactor ? c_mul(w0, __ldg(td + r * E + t))
-                                         : __ldg(a.mix_tw + (size_t)r * N + K);
-                x[t] = c_add(x[t], c_mul(er[2 * xpad_s<SH>(K & (NP - 1))], w));
+                const int kk = 2 * xpad_s<SH>(K & (NP - 1));
+                float2 acc = eb[kk];                                         // r = 0
+                if (a.n_sb > 1) {
+                    const float2 w1 = c_mul(wk0, __ldg(td + E + t));         // W_N^K
+                    float2 w = w1;
+#pragma unroll
+                    for (int r = 1; r < kMaxBands32; ++r) {
+                        if (r < a.n_sb) {
+                            acc = c_add(acc, c_mul(eb[r * XLg + kk], w));
+                            if (r + 1 < a.n_sb) w = c_mul(w, w1);
+                        }
+                    }
+                }
+                x[t] = acc;
             }
         }
     }
@@ -657,15 +686,36 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         // W_N^(K r) = W_N^((j + NP q) r) W_N^((N'/E) t r): one table load per q and thread
         const float2* wr = a.mix_tw + (size_t)gi * N;
         const float2* tm = a.mix_tm + gi * E;                      // [n_sb][E], row gi
+        if constexpr (kFactor) {
 #pragma unroll
-        for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
-        for (int q = 0; q < a.n_sb; ++q) {
-            const float2 w0 = __ldg(wr + j + NP * q);
+            for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
+            for (int q = 0; q < a.n_sb; ++q) {
+                const float2 w0 = __ldg(wr + j + NP * q);
+#pragma unroll
+                for (int t = 0; t < E; ++t) {
+                    const int K = j + TPF * t + NP * q;
+                    x[t] = c_add(x[t], c_mulc(ex[2 * xpad_s<SH>(K)], c_mul(w0, __ldg(tm + t))));
+                }
+            }
+        } else {
+            // 32 slots, as in the DEMUX: W_N^(K gi) = W_N^((j + (N'/E) t) gi) W_N^(N' q gi), the
+            // first factor from one gather and slot t's factor, the second as powers of
+            // W_N^(N' gi)
+            const float2 a0 = __ldg(wr + j);                                  // W_N^(j gi)
+            const float2 b1 = a.n_sb > 1 ? __ldg(wr + NP) : make_float2(1.f, 0.f);
 #pragma unroll
             for (int t = 0; t < E; ++t) {
-                const int K = j + TPF * t + NP * q;
-                const float2 w = kFactor ? c_mul(w0, __ldg(tm + t)) : __ldg(wr + K);   // as above
-                x[t] = c_add(x[t], c_mulc(ex[2 * xpad_s<SH>(K)], w));
+                const int K0t = j + TPF * t;
+                float2 w = c_mul(a0, __ldg(tm + t));                         // q = 0
+                float2 acc = c_mulc(ex[2 * xpad_s<SH>(K0t)], w);
+#pragma unroll
+                for (int q = 1; q < kMaxBands32; ++q) {
+                    if (q < a.n_sb) {
+                        w = c_mul(w, b1);
+                        acc = c_add(acc, c_mulc(ex[2 * xpad_s<SH>(K0t + NP * q)], w));
+                    }
+                }
+                x[t] = acc;
             }
         }
     }
