@@ -320,9 +320,12 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
     constexpr int CSH = 4;
     constexpr int CSL = NP + (NP >> CSH);              // float2 per (cos, sin) row
     // DEMUX/MUX twiddles: 16 slots, one table value per polyphase row times a per-slot factor;
-    // 32 slots, one table value per thread and per-slot factors, the rows by powers (see below)
+    // 32 slots of N' = 1024, one table value per thread and per-slot factors, the rows by powers
+    // (see below); N' = 2048 reads every twiddle from the table (its 64 threads per group leave
+    // no registers for the products: the powers took c5 from 1.651 to 1.689 ms)
     constexpr bool kFactor = E == 16;
-    // 32-slot plans have at most 5 subbands (2 x 5 x N'/32 threads fill the CTA)
+    constexpr bool kPowers = E == 32 && NP == 1024;
+    // 32-slot plans of N' = 1024 have at most 5 subbands (2 x 5 x 32 threads fill the CTA)
     constexpr int kMaxBands32 = 5;
     const int TB = tp.TB, g = tp.g, rem = tp.rem, p = tp.p, gi = tp.gi, j = tp.j;
     unsigned char* region = smem + (size_t)g * region_bytes;
@@ -464,7 +467,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         const float2* td = a.mix_td;                                    // [n_sb][E]
         int K0 = ci + j;
         K0 += (K0 < 0) ? N : 0;
-        if constexpr (kFactor) {
+        if constexpr (!kPowers) {
 #pragma unroll
             for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
             for (int r = 0; r < a.n_sb; ++r) {
@@ -475,12 +478,13 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
                     const int kap = j + TPF * t;
                     int K = ci + (kap < NP / 2 ? kap : kap - NP);
                     K += (K < 0) ? N : 0;
-                    const float2 w = c_mul(w0, __ldg(td + r * E + t));
+                    const float2 w = kFactor ? c_mul(w0, __ldg(td + r * E + t))
+                                             : __ldg(a.mix_tw + (size_t)r * N + K);
                     x[t] = c_add(x[t], c_mul(er[2 * xpad_s<SH>(K & (NP - 1))], w));
                 }
             }
         } else {
-            // 32 slots: slot t outermost, so only the finished slots' sums stay live, and
+            // N' = 1024: slot t outermost, so only the finished slots' sums stay live, and
             // W_N^(K r) as the powers of W_N^K = W_N^(K_0) times slot t's row-1 factor: one
             // table gather per thread instead of one per (r, t) (at most 4 products deep)
             const float2 wk0 =
@@ -686,7 +690,7 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
         // W_N^(K r) = W_N^((j + NP q) r) W_N^((N'/E) t r): one table load per q and thread
         const float2* wr = a.mix_tw + (size_t)gi * N;
         const float2* tm = a.mix_tm + gi * E;                      // [n_sb][E], row gi
-        if constexpr (kFactor) {
+        if constexpr (!kPowers) {
 #pragma unroll
             for (int t = 0; t < E; ++t) x[t] = make_float2(0.f, 0.f);
             for (int q = 0; q < a.n_sb; ++q) {
@@ -694,11 +698,12 @@ __device__ __forceinline__ bool chain_block(const ChainArgs& a, unsigned char* s
 #pragma unroll
                 for (int t = 0; t < E; ++t) {
                     const int K = j + TPF * t + NP * q;
-                    x[t] = c_add(x[t], c_mulc(ex[2 * xpad_s<SH>(K)], c_mul(w0, __ldg(tm + t))));
+                    const float2 w = kFactor ? c_mul(w0, __ldg(tm + t)) : __ldg(wr + K);
+                    x[t] = c_add(x[t], c_mulc(ex[2 * xpad_s<SH>(K)], w));
                 }
             }
         } else {
-            // 32 slots, as in the DEMUX: W_N^(K gi) = W_N^((j + (N'/E) t) gi) W_N^(N' q gi), the
+            // N' = 1024, as in the DEMUX: W_N^(K gi) = W_N^((j + (N'/E) t) gi) W_N^(N' q gi), the
             // first factor from one gather and slot t's factor, the second as powers of
             // W_N^(N' gi)
             const float2 a0 = __ldg(wr + j);                                  // W_N^(j gi)
