@@ -193,8 +193,9 @@ def form_batched(steps: int, warmup: int):
     """Batching form: 256 uneven realizations of the c1 signal model (lengths log-uniform 2^12 ..
     2^17 symbols, steps in {1,2,4,8,15}, subbands in {1,3,5}, N' and overlap from the autotuner
     in measure mode: each job shape's candidates timed on this GPU, the paper's operation count
-    having proved a poor guide to the kernel's time at small N') as one CUDA-graph replay of the
-    persistent per-group launches, next to the same jobs as sequential plain launches."""
+    having proved a poor guide to the kernel's time at small N'; one N' per subband count, so
+    one persistent launch per count) as one CUDA-graph replay of the persistent per-group
+    launches, next to the same jobs as sequential plain launches."""
     import dataclasses
     import tempfile
     import torch
@@ -205,9 +206,14 @@ def form_batched(steps: int, warmup: int):
     w0 = lk.gamma * signals.effective_length(lk.alpha, lk.span_length)
     link = cbessfm.make_link(lk.beta2, lk.span_length, lk.n_spans, sig.sample_rate)
     jobs, sym2d, flops = [], 0, 0.0
-    for k, jb in enumerate(signals.batch_jobs_c3(wl.seed)):
-        n_fft, ov = tuner.choose(autotune.JobShape(jb["n_sb"], jb["n_st"], d.ntaps, lk.beta2,
-                                                   lk.length, sig.sample_rate))
+    spec = list(signals.batch_jobs_c3(wl.seed))
+    # one N' per subband count (one persistent launch each), chosen on the summed measured
+    # time of that count's jobs
+    choices = tuner.choose_batch(
+        [autotune.JobShape(jb["n_sb"], jb["n_st"], d.ntaps, lk.beta2, lk.length, sig.sample_rate)
+         for jb in spec],
+        [float(jb["n_samples"]) for jb in spec])
+    for jb, (n_fft, ov) in zip(spec, choices):
         w = wl.with_(signal=dataclasses.replace(sig, n_sym=jb["n_samples"] // 2))
         tx, _ = signals.tx_waveform(w, 0.0, seed=jb["seed"])
         taps = signals.random_taps(jb["seed"], jb["n_st"], jb["n_sb"], d.ntaps, w0 / jb["n_st"])
@@ -226,7 +232,8 @@ def form_batched(steps: int, warmup: int):
     t_plain = _events_ms(lambda: [pl.backpropagate(x, y) for pl, x, y in jobs], steps, warmup)
     info = batch.info()
     return {"workload": "c3_batched: 256 uneven c1-model realizations, 1x80 km, steps {1,2,4,8,15},"
-                        " subbands {1,3,5}, N' / overlap autotuned by measurement",
+                        " subbands {1,3,5}, N' / overlap autotuned by measurement (one N' per"
+                        " subband count)",
             "value": sym2d / (t_graph / 1e3), "unit": UNIT, "ms_per_step": t_graph,
             "sym2d_per_step": sym2d, "groups": info["groups"], "work_items": info["work_items"],
             "algorithmic_tflops": flops / (t_graph / 1e3) / 1e12,

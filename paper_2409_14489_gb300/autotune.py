@@ -11,7 +11,9 @@ For each job shape (subbands, steps, taps, link, sample rate, storage) it picks:
   2D symbol (Eq. (costRM) plus its RA companion) instead and needs no GPU.
 
 Measured choices are cached in a JSON file (``$CBESSFM_AUTOTUNE_CACHE`` or ``_build/autotune.json``
-next to this file), keyed by the job shape.
+next to this file), keyed by the job shape.  ``choose_batch`` picks for a whole batch: one N'
+per subband count (the batched form's launch groups), the one with the least summed cost over
+the group's jobs.
 """
 from __future__ import annotations
 
@@ -19,7 +21,7 @@ import json
 import math
 import os
 from dataclasses import dataclass
-from typing import Dict, Optional, Tuple
+from typing import Dict, List, Optional, Sequence, Tuple
 
 from . import cost
 
@@ -90,6 +92,7 @@ class Autotuner:
         self.cache_path = cache_path or os.environ.get(
             "CBESSFM_AUTOTUNE_CACHE", os.path.join(_HERE, "_build", "autotune.json"))
         self.cache: Dict[str, Tuple[int, int]] = {}
+        self.times: Dict[str, Dict[Tuple[int, int], float]] = {}
         if mode == "measure" and os.path.exists(self.cache_path):
             try:
                 with open(self.cache_path) as f:
@@ -117,7 +120,52 @@ class Autotuner:
 
     def _measure(self, shape: JobShape, cands):
         times = measure_candidates(shape, cands)
+        self.times[shape.key()] = times
         return min(times, key=times.get)
+
+    def candidate_costs(self, shape: JobShape) -> Dict[Tuple[int, int], float]:
+        """Per-candidate cost per valid sample: measured time (ms, timed once per shape and kept
+        for the tuner's life) in measure mode, the paper's operation count in model mode."""
+        cands = candidates(shape)
+        if self.mode == "model":
+            return {c: model_cost(shape, *c) for c in cands}
+        k = shape.key()
+        if k not in self.times:
+            self.times[k] = measure_candidates(shape, cands)
+        return self.times[k]
+
+    def choose_batch(self, shapes: Sequence[JobShape],
+                     weights: Sequence[float]) -> List[Tuple[int, int]]:
+        """(N', N'_ov) for every job of a batch, one N' per subband count and storage type.
+
+        The batched form runs one persistent launch per (N', subbands, storage) group, and a
+        group with few work items leaves SMs idle while its last CTAs finish, so choosing each
+        job shape's own fastest N' can make the batch slower than a common choice.  Per group of
+        jobs that share a subband count and storage type, this picks the N' that minimizes the
+        summed cost, each job's cost per valid sample (``candidate_costs``) times its weight
+        (its valid samples); each job keeps its own overlap for that N'."""
+        if len(shapes) != len(weights):
+            raise ValueError("one weight per shape")
+        groups: Dict[Tuple[int, int], List[int]] = {}
+        for i, sh in enumerate(shapes):
+            groups.setdefault((sh.n_sb, sh.storage), []).append(i)
+        out: List[Optional[Tuple[int, int]]] = [None] * len(shapes)
+        for idx in groups.values():
+            costs = [self.candidate_costs(shapes[i]) for i in idx]
+            common = set.intersection(*({c[0] for c in cs} for cs in costs))
+            if not common:                          # no shared N': each job on its own
+                for i, cs in zip(idx, costs):
+                    out[i] = min(cs, key=cs.get)
+                continue
+
+            def total(nf):
+                return sum(weights[i] * next(v for c, v in cs.items() if c[0] == nf)
+                           for i, cs in zip(idx, costs))
+
+            best = min(sorted(common), key=total)
+            for i, cs in zip(idx, costs):
+                out[i] = next(c for c in cs if c[0] == best)
+        return out  # type: ignore[return-value]
 
 
 def measure_candidates(shape: JobShape, cands=None, reps: int = 3) -> Dict[Tuple[int, int], float]:

@@ -92,3 +92,42 @@ def test_block_limits_agree_with_the_library():
                 L.cbessfm_plan_destroy(h)
             assert st in (cb.OK, cb.ERR_CUDA, cb.ERR_UNSUPPORTED), (nf, n_sb, st)
             assert (st != cb.ERR_UNSUPPORTED) == autotune._block_fits(nf, n_sb), (nf, n_sb)
+
+
+def test_batch_choice_is_one_block_size_per_subband_count(tmp_path):
+    """choose_batch: jobs sharing a subband count get one N' (one persistent launch), the one
+    with the least weighted summed cost, even where a job's own fastest N' differs; each job
+    keeps its own overlap.  Measured costs are planted, so no GPU is touched."""
+    tuner = autotune.Autotuner("measure", cache_path=str(tmp_path / "t.json"))
+    a = _shape(n_sb=3, n_st=1, L=80e3, R=192e9)
+    b = _shape(n_sb=3, n_st=15, L=80e3, R=192e9)
+    c = _shape(n_sb=1, n_st=4, L=80e3, R=64e9)
+    ov3 = autotune.overlap_for(a)
+    ov1 = autotune.overlap_for(c)
+    # a alone prefers 512, b alone prefers 1024; with b weighted 3x, 1024 wins the group:
+    # 1 x 1.00 + 3 x 1.00 = 4.00 (1024) against 1 x 0.95 + 3 x 1.10 = 4.25 (512)
+    tuner.times[a.key()] = {(256, ov3): 1.30, (512, ov3): 0.95, (1024, ov3): 1.00, (2048, ov3): 1.40}
+    tuner.times[b.key()] = {(256, ov3): 1.20, (512, ov3): 1.10, (1024, ov3): 1.00, (2048, ov3): 1.30}
+    tuner.times[c.key()] = {(nf, ov1): t for nf, t in ((256, 2.0), (512, 1.0), (1024, 1.2),
+                                                       (2048, 1.5))}
+    got = tuner.choose_batch([a, b, c, b], [1.0, 1.5, 7.0, 1.5])
+    assert got == [(1024, ov3), (1024, ov3), (512, ov1), (1024, ov3)]
+    # with a weighted up instead, the group moves to a's choice
+    assert tuner.choose_batch([a, b], [10.0, 1.0]) == [(512, ov3), (512, ov3)]
+    with pytest.raises(ValueError):
+        tuner.choose_batch([a], [1.0, 2.0])
+
+
+def test_batch_choice_in_model_mode_minimizes_the_summed_operation_count():
+    tuner = autotune.Autotuner("model")
+    shapes = [_shape(n_sb=5, n_st=n, L=80e3, R=320e9) for n in (1, 4, 15)]
+    weights = [3.0, 1.0, 2.0]
+    got = tuner.choose_batch(shapes, weights)
+    assert len({nf for nf, _ in got}) == 1
+    nfs = {c[0] for c in autotune.candidates(shapes[0])}
+
+    def total(nf):
+        return sum(w * next(autotune.model_cost(s, *c) for c in autotune.candidates(s)
+                            if c[0] == nf) for s, w in zip(shapes, weights))
+
+    assert total(got[0][0]) == min(total(nf) for nf in nfs)
