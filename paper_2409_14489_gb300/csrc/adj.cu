@@ -113,6 +113,7 @@ cudaError_t launch_np_adj(const ChainArgs& a, int threads, cudaStream_t st) {
     if (grid <= 0) return cudaSuccess;
     const size_t smem = (size_t)a.G * a.region_bytes;
     if (a.per_pol) return launch_adj_per_pol(NP, ADJ, a, threads, st);   // adj_perpol.cu
+    if (ADJ && a.want_ratio == 0) return launch_adj_taps(NP, a, threads, st);   // adj_taps.cu
     if constexpr (ADJ) {
         const size_t smem_a = smem + chain_tw_bytes(fft_tw_size(NP));   // + staged twiddles
         cudaError_t e = cudaFuncSetAttribute(cbessfm_adj_kernel<NP>,

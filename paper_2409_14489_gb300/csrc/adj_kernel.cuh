@@ -45,6 +45,12 @@ __device__ __forceinline__ void fir8_acc(const ChainArgs& a, const float4* __res
     }
 }
 
+// Start moving `bytes` of global memory (16-byte aligned, a multiple of 16 bytes) into L2
+// without waiting for them (a bulk prefetch; no completion to track).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // write value v of row sample n (and its circular halo copies) into swizzled row `row`
 template <int NP, int E>
 __device__ __forceinline__ void row_store(float* row, int mb, int n, int H, float v) {
@@ -62,7 +68,10 @@ __device__ __forceinline__ void row_store(float* row, int mb, int n, int H, floa
 //   dL/dw_il[m] = sum_k S_i[k] P_l[k - m] + [i != l] (1/3) sum_k D_i[k] (Px_l - Py_l)[k - m].
 // The phase row then holds (theta^x, theta^y) per sample, and each polarization thread forms
 // its own exp(j theta^p) - 1.
-template <int NP, bool PERPOL = false>
+// RHO = false compiles the form without the ratio gradient (the taps-only launch of the Manakov
+// form, adj_taps.cu), which also asks L2 for each step's checkpoint a step ahead.  RHO = true
+// keeps the ratio work under the run-time flag a.want_ratio.
+template <int NP, bool PERPOL = false, bool RHO = true>
 __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) {
     constexpr int E = fft_slots(NP);
     constexpr int TPF = NP / E;
@@ -105,6 +114,16 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     const long long gblk = real ? item : 0;
     const GroupBar<NP, E> bar{1 + g * n_sb + gi};
     const float2* ck = a.ckpt + (size_t)gblk * (size_t)(a.n_st + 2) * 2 * N + (size_t)gi * NP * 2 + p;
+    // taps-only form: one thread per block asks L2 for a step's checkpoint of time samples
+    // (field c, 16 N bytes) a step ahead, so that the step's first read of it does not wait on
+    // HBM (c4: 1.541 -> 1.503 ms; in the ratio form the same code slowed the launch)
+    const float2* const ck_block = a.ckpt + (size_t)gblk * (size_t)(a.n_st + 2) * 2 * N;
+    auto prefetch_ckpt = [&](int c) {
+        if constexpr (!RHO) {
+            if (real && rem == 0) prefetch_l2(ck_block + (size_t)c * 2 * N, 16u * (uint32_t)N);
+        }
+    };
+    if (a.n_st > 0) prefetch_ckpt(a.n_st);                // the last step's, used first
     auto load_ckpt = [&](int c, float2 (&v)[E]) {
         const float2* src = ck + (size_t)c * 2 * N;
 #pragma unroll
@@ -201,12 +220,13 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
     for (int s = a.n_st - 1; s >= 0; --s) {
         const float2* h = a.gvd + (size_t)((s < a.n_st - 1 ? 1 : 2) * n_sb + gi) * NP;
         // G_W = conj(h) G_(Z_(s+1)), kept in the block's scratch when dL/drho is wanted
-        const bool rho = a.want_ratio != 0;
+        const bool rho = RHO && a.want_ratio != 0;
 #pragma unroll
         for (int t = 0; t < E; ++t) {
             x[t] = c_mulc(x[t], __ldg(h + j + TPF * t));
             if (real && rho) sg[2 * (j + TPF * t)] = x[t];
         }
+        if (s > 0) prefetch_ckpt(s);                       // the next step's (c = 1 + (s - 1))
         {
             float2 u[E];
             load_ckpt(1 + s, u);
@@ -563,5 +583,7 @@ __global__ void __launch_bounds__(640, 1) cbessfm_adj_kernel(const ChainArgs a) 
 // false) or the adjoint kernel over the blocks of `a`, with the region sizes set in `a`.
 cudaError_t launch_adj_per_pol(int np, bool adjoint, const ChainArgs& a, int threads,
                                cudaStream_t st);
+// Launch of the Manakov adjoint without the ratio gradient (adj_taps.cu).
+cudaError_t launch_adj_taps(int np, const ChainArgs& a, int threads, cudaStream_t st);
 
 }  // namespace cbessfm
